@@ -1,0 +1,58 @@
+"""Named synthetic workloads (sizes, ranges and seeds of the measured configs).
+
+Network seed 2312 and cell seed 4998 throughout.  Times are in seconds.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+YEAR = 3.15576e7
+NET_SEED = 2312
+CELL_SEED = 4998
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n_s: int
+    n_r: int
+    cells: int
+    T: object
+    nH: object
+    Av: object
+    start: str            # "atomic" or "loguniform"
+    t_end: float = 0.0
+    rtol: float = 1e-6
+    atol: float = 1e-20
+
+
+WORKLOADS = {
+    "single_cell_32x180": Workload("single_cell_32x180", 32, 180, 1, 10.0, 1e4, 5.0,
+                                   "atomic", 1e6 * YEAR),
+    "rhs_jac_470x6000_c4096": Workload("rhs_jac_470x6000_c4096", 470, 6000, 4096,
+                                       (10.0, 300.0), (1e2, 1e7), (0.0, 10.0), "loguniform"),
+    "integrate_470x6000_c65536": Workload("integrate_470x6000_c65536", 470, 6000, 65536,
+                                          (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0),
+                                          "atomic", 1e6 * YEAR),
+    "adjoint_470x6000_c1024": Workload("adjoint_470x6000_c1024", 470, 6000, 1024,
+                                       (10.0, 300.0), (1e2, 1e7), (0.0, 10.0),
+                                       "atomic", 1e5 * YEAR),
+    "mixed_470x6000_c16384": Workload("mixed_470x6000_c16384", 470, 6000, 16384,
+                                      (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0),
+                                      "atomic", 1e6 * YEAR),
+}
+
+
+def make(name, cells=None):
+    """(desc, T, nH, Av, y0) for a named workload, optionally on fewer cells."""
+    from . import cells as _cells
+    from .network import generate
+    w = WORKLOADS[name]
+    C = w.cells if cells is None else cells
+    desc = generate(NET_SEED, w.n_s, w.n_r)
+    T, nH, Av = _cells.conditions(CELL_SEED, C, w.T, w.nH, w.Av)
+    if w.start == "atomic":
+        y0 = _cells.atomic_start(desc, C)
+    else:
+        y0 = _cells.loguniform_abundances(desc, CELL_SEED, C)
+    return desc, T, nH, Av, y0
