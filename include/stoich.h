@@ -1,0 +1,174 @@
+/*
+ * stoich.h - C ABI of the GB300 (sm_103a) stoichiometry-matrix chemistry library.
+ *
+ * The library evaluates, for many independent hydro cells at once, the chemical
+ * right-hand side dx/dt = S R(x) of the paper's matrix formulation (Eq. 7, with
+ * S the species x reaction stoichiometry matrix and R_j = k'_j prod x_reactants,
+ * Eqs. 2-6), its Jacobian J = S dR/dx, and a BDF/Newton stiff integrator that
+ * consumes them (the role DLSODES plays in Section 3).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an sm_status (SM_OK == 0) and never aborts, traps
+ *    or exits; sm_status_str() gives a message.
+ *  - Batched arrays are species-major (or reaction-major) with the CELL index
+ *    fastest: element (i, c) of an [n][ld] array lives at i*ld + c, with
+ *    C <= ld.  ld must be a multiple of 32 (coalesced 256-byte rows).
+ *  - Pointers named d_* are DEVICE pointers on the network's device, owned by
+ *    the caller; the library never frees them.  Pointers named h_* are host
+ *    pointers.  Handles (sm_net, sm_state) and their internal device buffers
+ *    are owned by the library and released by the matching *_free call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device calls are asynchronous on that stream; errors raised inside a
+ *    kernel are written to a device status word and reported by sm_sync() or
+ *    by the next synchronous call on the same handle.
+ *  - Sizes: C >= 0; C == 0 is a valid no-op.
+ */
+#ifndef STOICH_H
+#define STOICH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sm_status;
+enum {
+    SM_OK = 0,
+    SM_EINVAL = 1,     /* bad argument (null pointer, size, layout, enum)       */
+    SM_ENOMEM = 2,     /* device or host allocation failed                      */
+    SM_ECUDA = 3,      /* a CUDA runtime call failed                            */
+    SM_ENOTCONS = 4,   /* network does not conserve elements / charge (E.S!=0)  */
+    SM_ETIMEOUT = 5,   /* a bounded device wait ran out                         */
+    SM_EPARTIAL = 6,   /* the call completed but some cells failed (see stats)  */
+    SM_ENOTSUP = 7     /* combination not supported                             */
+};
+
+/* Per-cell integration status (sm_cell_stats.status). */
+enum {
+    SM_CELL_OK = 0,
+    SM_CELL_MAXSTEPS = 1,  /* max_steps accepted steps taken before t_end       */
+    SM_CELL_HMIN = 2,      /* step size fell below the time resolution          */
+    SM_CELL_CONV = 3,      /* repeated Newton convergence failures              */
+    SM_CELL_NAN = 4,       /* non-finite input or state                         */
+    SM_CELL_RUNNING = 5    /* not finished yet (integration continues)          */
+};
+
+/* Reaction classes and their rate laws (rates are evaluated once per cell,
+ * outside the solver, as in Section 3):
+ *   SM_TWO_BODY, SM_DISS_RECOMB: k = alpha (T/300)^beta exp(-gamma/T), k' = k n_H
+ *   SM_COSMIC_RAY:               k = alpha zeta,                        k' = k
+ *   SM_PHOTO:                    k = alpha exp(-gamma A_V),             k' = k   */
+enum { SM_TWO_BODY = 0, SM_COSMIC_RAY = 1, SM_PHOTO = 2, SM_DISS_RECOMB = 3 };
+
+/* Storage formats of S (Section 2.2, Listings 1-4) and row orders (Section 3). */
+enum { SM_FMT_CRS = 0, SM_FMT_COO = 1, SM_FMT_CCS = 2, SM_FMT_SELL = 3 };
+enum { SM_ORDER_NONE = 0, SM_ORDER_NNZ = 1, SM_ORDER_RCM = 2 };
+
+/* Explicit network description (host arrays, read during sm_net_build only).
+ *   comp      int32 [n_s][n_elem+1]: atoms of each element, last column = charge
+ *   reactants int32 [n_r][2]: species indices, -1 padded (first entry >= 0);
+ *             a species listed twice reacts with multiplicity two
+ *   products  int32 [n_r][4]: species indices, -1 padded
+ *   rclass    int8  [n_r]: SM_TWO_BODY ... SM_DISS_RECOMB
+ *   alpha, beta, gamma double [n_r]: rate parameters (see the class enum)   */
+typedef struct {
+    int32_t n_s, n_r, n_elem;
+    const int32_t* comp;
+    const int32_t* reactants;
+    const int32_t* products;
+    const int8_t* rclass;
+    const double* alpha;
+    const double* beta;
+    const double* gamma;
+} sm_net_desc;
+
+typedef struct sm_net sm_net;
+
+/* Network statistics and per-cell algorithmic work of the batched kernels. */
+typedef struct {
+    int32_t n_s, n_r;
+    int64_t nnz_S;          /* nonzeros of S (net coefficients)                 */
+    int64_t nnz_J;          /* structural nonzeros of J, diagonal included      */
+    int64_t n_jac_terms;    /* sum over J entries of contributing reactions     */
+    int64_t nnz_LU;         /* nonzeros of L+U after symbolic factorisation     */
+    int64_t lu_flops;       /* flops of one numeric factorisation (2 per FMA)   */
+    int32_t lu_head;        /* pivots eliminated as sparse before the dense tail */
+    int32_t max_row_nnz;    /* longest row of S (the H row in the paper)        */
+    int32_t fmt, order, sell_C, sell_sigma; /* current traversal format        */
+    int64_t fmt_entries;    /* stored entries of the current format (pads incl.) */
+    double rhs_bytes;       /* per cell: 8 (n_r + 2 n_s)                        */
+    double rhs_flops;       /* per cell: 2 nnz_S + sum_j order_j                */
+    double jac_bytes;       /* per cell: 8 (n_r + n_s + nnz_J)                  */
+    double jac_flops;       /* per cell: 2 n_jac_terms + sum_j order_j          */
+} sm_net_info;
+
+/* Build a network on `device` from an explicit description: validates indices
+ * and classes (SM_EINVAL) and conservation E.S = 0 (SM_ENOTCONS); builds S
+ * (Eq. 7: products minus reactants, zero net entries dropped), the traversal
+ * formats, the Jacobian pattern and the symbolic LU, and uploads them once.
+ * The default traversal is CRS in the original order.  *out receives a handle
+ * owned by the caller until sm_net_free. */
+sm_status sm_net_build(const sm_net_desc* d, int32_t device, sm_net** out);
+sm_status sm_net_free(sm_net* net);
+
+/* Select the traversal used by sm_rhs_eval: fmt (SM_FMT_*), row order
+ * (SM_ORDER_*; nnz = descending nonzero count, stable, Section 3; RCM =
+ * reverse Cuthill-McKee on pattern(S S^T)), and for SELL the slice height C
+ * (1..32) and sorting window sigma (>= 1).  Results do not depend on the
+ * choice beyond floating-point summation order. */
+sm_status sm_net_set_format(sm_net* net, int32_t fmt, int32_t order, int32_t sell_C,
+                            int32_t sell_sigma);
+sm_status sm_net_get_info(const sm_net* net, sm_net_info* info);
+
+/* Export host copies of internal structures for bit-exact checks.  what:
+ *  SM_X_ROW_ORDER int32[n_s]    rows (species) in traversal order
+ *  SM_X_COL_ORDER int32[n_r]    columns (reactions) in traversal order
+ *  SM_X_FMT_PTR   int32[]       CRS row_ptr / CCS col_ptr / SELL slice_ptr (COO: none)
+ *  SM_X_FMT_IDX   int32[]       CRS col_ind / CCS row_ind / COO row_ind / SELL col_ind
+ *  SM_X_FMT_IDX2  int32[]       COO col_ind / SELL row_id (-1 = padding row)
+ *  SM_X_FMT_VAL   double[]      coefficients (0 at SELL pads)
+ *  SM_X_FMT_LEN   int32[]       SELL slice lengths
+ *  SM_X_JPAT_PTR  int32[n_s+1]  CRS row pointer of the Jacobian pattern
+ *  SM_X_JPAT_COL  int32[nnz_J]  its column indices (ascending per row)
+ *  SM_X_LU_PERM   int32[n_s]    elimination order of the Newton matrix
+ * sm_net_export_size() returns the byte size; sm_net_export() copies exactly
+ * that many bytes into h_buf (SM_EINVAL if `bytes` is smaller). */
+enum {
+    SM_X_ROW_ORDER = 0, SM_X_COL_ORDER = 1, SM_X_FMT_PTR = 2, SM_X_FMT_IDX = 3,
+    SM_X_FMT_IDX2 = 4, SM_X_FMT_VAL = 5, SM_X_FMT_LEN = 6, SM_X_JPAT_PTR = 7,
+    SM_X_JPAT_COL = 8, SM_X_LU_PERM = 9
+};
+sm_status sm_net_export_size(const sm_net* net, int32_t what, size_t* bytes);
+sm_status sm_net_export(const sm_net* net, int32_t what, void* h_buf, size_t bytes);
+
+/* Rate coefficients k'[n_r][ld] (FP64) for C cells with temperature d_T[C] (K),
+ * density d_nH[C] (cm^-3) and visual extinction d_Av[C]; zeta is the
+ * cosmic-ray ionisation rate (s^-1).  Rate laws: see the class enum.  Computed
+ * as exp(log alpha + beta log(T/300) - gamma/T) n_H for two-body classes, so
+ * results differ from alpha (T/300)^beta exp(-gamma/T) n_H by rounding only. */
+sm_status sm_rates_eval(const sm_net* net, int64_t C, const double* d_T, const double* d_nH,
+                        const double* d_Av, double zeta, double* d_k, int64_t ld, void* stream);
+
+/* Right-hand side f = S R(y) (Eq. 7) for C cells: d_k = k'[n_r][ld], d_y =
+ * x[n_s][ld] -> d_f[n_s][ld], FP64, with the traversal chosen by
+ * sm_net_set_format.  d_f must not alias d_k or d_y. */
+sm_status sm_rhs_eval(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
+                      double* d_f, int64_t ld, void* stream);
+
+/* Jacobian values J = S dR/dx on the static pattern (SM_X_JPAT_*): d_J is
+ * [nnz_J][ld], entry p of the pattern for cell c at p*ld + c, FP64. */
+sm_status sm_jac_eval(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
+                      double* d_J, int64_t ld, void* stream);
+
+/* Wait for all work on `stream` and report (and clear) any error a kernel of
+ * this network wrote to its device status word. */
+sm_status sm_sync(const sm_net* net, void* stream);
+
+const char* sm_status_str(sm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOICH_H */

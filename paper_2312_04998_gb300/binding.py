@@ -1,0 +1,195 @@
+"""Thin ctypes binding of libstoich.so (include/stoich.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream; batched
+arrays are [n][ld] tensors (cells fastest, ld a multiple of 32) of which the
+first C columns are used.  If the library is missing the import fails loudly;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstoich.so")
+
+SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ENOTCONS, SM_ETIMEOUT, SM_EPARTIAL, SM_ENOTSUP = range(8)
+FMT = {"crs": 0, "coo": 1, "ccs": 2, "sell": 3}
+ORDER = {"none": 0, "nnz": 1, "rcm": 2}
+X_ROW_ORDER, X_COL_ORDER, X_FMT_PTR, X_FMT_IDX, X_FMT_IDX2, X_FMT_VAL, X_FMT_LEN, \
+    X_JPAT_PTR, X_JPAT_COL, X_LU_PERM = range(10)
+
+
+class StoichError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {status_str(code)} (status {code})")
+        self.code = code
+
+
+class NetDesc_c(ct.Structure):
+    _fields_ = [("n_s", ct.c_int32), ("n_r", ct.c_int32), ("n_elem", ct.c_int32),
+                ("comp", ct.POINTER(ct.c_int32)), ("reactants", ct.POINTER(ct.c_int32)),
+                ("products", ct.POINTER(ct.c_int32)), ("rclass", ct.POINTER(ct.c_int8)),
+                ("alpha", ct.POINTER(ct.c_double)), ("beta", ct.POINTER(ct.c_double)),
+                ("gamma", ct.POINTER(ct.c_double))]
+
+
+class NetInfo_c(ct.Structure):
+    _fields_ = [("n_s", ct.c_int32), ("n_r", ct.c_int32), ("nnz_S", ct.c_int64),
+                ("nnz_J", ct.c_int64), ("n_jac_terms", ct.c_int64), ("nnz_LU", ct.c_int64),
+                ("lu_flops", ct.c_int64), ("lu_head", ct.c_int32), ("max_row_nnz", ct.c_int32),
+                ("fmt", ct.c_int32), ("order", ct.c_int32), ("sell_C", ct.c_int32),
+                ("sell_sigma", ct.c_int32), ("fmt_entries", ct.c_int64), ("rhs_bytes", ct.c_double),
+                ("rhs_flops", ct.c_double), ("jac_bytes", ct.c_double), ("jac_flops", ct.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point.
+_SIGS = [
+    ("sm_status_str", ct.c_char_p, [ct.c_int32]),
+    ("sm_net_build", ct.c_int32, [ct.POINTER(NetDesc_c), ct.c_int32, ct.POINTER(ct.c_void_p)]),
+    ("sm_net_free", ct.c_int32, [ct.c_void_p]),
+    ("sm_net_set_format", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]),
+    ("sm_net_get_info", ct.c_int32, [ct.c_void_p, ct.POINTER(NetInfo_c)]),
+    ("sm_net_export_size", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_size_t)]),
+    ("sm_net_export", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_size_t]),
+    ("sm_rates_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                   ct.c_double, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    ("sm_rhs_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                 ct.c_int64, ct.c_void_p]),
+    ("sm_jac_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                 ct.c_int64, ct.c_void_p]),
+    ("sm_sync", ct.c_int32, [ct.c_void_p, ct.c_void_p]),
+]
+
+
+def lib():
+    """Load libstoich.so once; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ct.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    return lib().sm_status_str(int(code)).decode()
+
+
+def _check(code, what):
+    if code != SM_OK:
+        raise StoichError(code, what)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ct.POINTER(ctype))
+
+
+def _dptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def pad_ld(C: int) -> int:
+    return max(32, (int(C) + 31) // 32 * 32)
+
+
+class Network:
+    """An uploaded network (sm_net).  device=-1 builds host structures only
+    (formats, orders, Jacobian pattern) for inspection without a GPU."""
+
+    def __init__(self, desc, device: int = 0):
+        L = lib()
+        self._keep = dict(
+            comp=np.ascontiguousarray(desc.comp, dtype=np.int32),
+            reac=np.ascontiguousarray(desc.reactants, dtype=np.int32),
+            prod=np.ascontiguousarray(desc.products, dtype=np.int32),
+            cls=np.ascontiguousarray(desc.rclass, dtype=np.int8),
+            alpha=np.ascontiguousarray(desc.alpha, dtype=np.float64),
+            beta=np.ascontiguousarray(desc.beta, dtype=np.float64),
+            gamma=np.ascontiguousarray(desc.gamma, dtype=np.float64))
+        k = self._keep
+        n_s, n_r = k["comp"].shape[0], k["reac"].shape[0]
+        d = NetDesc_c(n_s, n_r, k["comp"].shape[1] - 1, _ptr(k["comp"], ct.c_int32),
+                      _ptr(k["reac"], ct.c_int32), _ptr(k["prod"], ct.c_int32),
+                      _ptr(k["cls"], ct.c_int8), _ptr(k["alpha"], ct.c_double),
+                      _ptr(k["beta"], ct.c_double), _ptr(k["gamma"], ct.c_double))
+        h = ct.c_void_p()
+        _check(L.sm_net_build(ct.byref(d), int(device), ct.byref(h)), "sm_net_build")
+        self.h = h
+        self.device = device
+        self.n_s, self.n_r = n_s, n_r
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sm_net_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_format(self, fmt="crs", order="none", C=1, sigma=1):
+        _check(lib().sm_net_set_format(self.h, FMT[fmt], ORDER[order], int(C), int(sigma)),
+               "sm_net_set_format")
+
+    def info(self) -> dict:
+        inf = NetInfo_c()
+        _check(lib().sm_net_get_info(self.h, ct.byref(inf)), "sm_net_get_info")
+        return {name: getattr(inf, name) for name, _ in NetInfo_c._fields_}
+
+    def export(self, what: int, dtype=np.int32) -> np.ndarray:
+        n = ct.c_size_t()
+        _check(lib().sm_net_export_size(self.h, what, ct.byref(n)), "sm_net_export_size")
+        out = np.empty(n.value // np.dtype(dtype).itemsize, dtype=dtype)
+        _check(lib().sm_net_export(self.h, what, out.ctypes.data_as(ct.c_void_p), n.value),
+               "sm_net_export")
+        return out
+
+    # ---- batched device calls: torch tensors [n][ld], first C columns used ----
+
+    def _ld(self, *tensors):
+        ld = tensors[0].stride(0)
+        for t in tensors:
+            if t.stride(0) != ld or t.stride(-1) != 1:
+                raise ValueError("batched tensors must share the row stride ld with unit column stride")
+        return ld
+
+    def rates_eval(self, T, nH, Av, k, C=None, zeta=1.3e-17):
+        C = T.shape[0] if C is None else C
+        _check(lib().sm_rates_eval(self.h, int(C), _dptr(T), _dptr(nH), _dptr(Av), float(zeta),
+                                   _dptr(k), int(self._ld(k)), _stream(k.device)), "sm_rates_eval")
+        return k
+
+    def rhs_eval(self, k, y, f, C):
+        ld = self._ld(k, y, f)
+        _check(lib().sm_rhs_eval(self.h, int(C), _dptr(k), _dptr(y), _dptr(f), int(ld),
+                                 _stream(f.device)), "sm_rhs_eval")
+        return f
+
+    def jac_eval(self, k, y, J, C):
+        ld = self._ld(k, y, J)
+        _check(lib().sm_jac_eval(self.h, int(C), _dptr(k), _dptr(y), _dptr(J), int(ld),
+                                 _stream(J.device)), "sm_jac_eval")
+        return J
+
+    def sync(self):
+        import torch
+        _check(lib().sm_sync(self.h, _stream(torch.device("cuda", self.device))), "sm_sync")

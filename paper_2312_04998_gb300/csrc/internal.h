@@ -1,0 +1,116 @@
+// Internal structures of the stoichiometry-matrix library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "stoich.h"
+
+// Device status word bits written by kernels (never trap).
+enum : int32_t {
+  DEV_ERR_NONE = 0,
+  DEV_ERR_BOUNDS = 1,   // an index check failed; the access was skipped
+  DEV_ERR_TIMEOUT = 2,  // a bounded wait ran out
+};
+
+#define SM_TRY_CUDA(expr)                                      \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) {                                   \
+      sm_set_last_cuda_error(_e, #expr);                       \
+      return (_e == cudaErrorMemoryAllocation) ? SM_ENOMEM : SM_ECUDA; \
+    }                                                          \
+  } while (0)
+
+void sm_set_last_cuda_error(cudaError_t e, const char* what);
+
+// Rate-law parameters of one reaction: (log alpha for two-body classes,
+// alpha otherwise; beta; gamma; class as a double).
+struct __align__(32) RatePar {
+  double x, y, z, w;
+};
+
+// A device allocation owned by a handle.
+struct DevArray {
+  void* p = nullptr;
+  size_t bytes = 0;
+  sm_status upload(const void* h, size_t n);
+  sm_status ensure(size_t n);  // grow (no copy) to at least n bytes
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Traversal format as uploaded: see the sm_net_export documentation.
+struct Format {
+  int32_t fmt = SM_FMT_CRS, order = SM_ORDER_NONE, C = 1, sigma = 1;
+  std::vector<int32_t> ptr, idx, idx2, len;
+  std::vector<double> val;
+  // Device-only companion indices: CRS row ids, CCS column ids, COO column
+  // per nonzero, SELL row ids (-1 = padding row).
+  std::vector<int32_t> aux;
+  // Packed device entries: column (or row) in the low 24 bits, signed
+  // coefficient in the high 8 bits.
+  std::vector<uint32_t> packed;
+  // CRS warp partition: per chunk the first nonzero (n_chunks + 1 entries).
+  std::vector<int32_t> chunk_nz;
+  DevArray d_ptr, d_packed, d_aux, d_chunk;
+};
+
+// Symbolic LU of the Newton matrix M = I - gamma J (no pivoting).
+struct LUSymbolic {
+  int32_t n = 0, ld = 0, head = 0;
+  std::vector<int32_t> perm, iperm;       // perm[p] = species at position p
+  std::vector<int32_t> lptr, lidx;        // per pivot: rows below it (positions)
+  std::vector<int32_t> uptr, uidx;        // per pivot: columns right of it
+  std::vector<int32_t> jpos;              // per J pattern entry: dense offset p*ld+q
+  int64_t nnz = 0, flops = 0;
+  DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_jpos, d_perm, d_iperm;
+};
+
+struct sm_net {
+  int device = 0;
+  int32_t n_s = 0, n_r = 0, n_elem = 0;
+  std::vector<int32_t> comp, reac, prod;
+  std::vector<int8_t> cls;
+  std::vector<double> alpha, beta, gamma;
+  std::vector<int32_t> order;  // reactants per reaction
+  // S in column-compressed form, original order, rows ascending.
+  std::vector<int32_t> s_colptr, s_row;
+  std::vector<int8_t> s_coef;
+  // Row orders and column orders for SM_ORDER_NONE / NNZ / RCM.
+  std::vector<int32_t> row_order[3], col_order[3];
+  Format cur;
+  // Jacobian pattern (CRS, species order) and contribution list per entry:
+  // term = coef * k'[j] * (partner >= 0 ? y[partner] : 1).
+  std::vector<int32_t> jp_ptr, jp_col, jt_ptr, jt_rx, jt_partner;
+  std::vector<int8_t> jt_coef;
+  LUSymbolic lu;
+  // Device copies used by the kernels.
+  DevArray d_reac;        // int2 per reaction: reactant indices (-1 = none)
+  DevArray d_rate;        // RatePar per reaction: (log alpha | alpha, beta, gamma, class)
+  DevArray d_jp_ptr, d_jt_ptr, d_jt_word;  // Jacobian gather lists
+  std::vector<int32_t> jchunk;             // J entries per gather chunk (balanced by terms)
+  DevArray d_jchunk;
+  DevArray d_status;      // int32 device status word
+  DevArray d_scratch;     // reaction-rate scratch for rhs_eval
+  sm_net_info info{};
+};
+
+// Host-side builders (net_build.cpp).
+sm_status net_build_host(const sm_net_desc* d, sm_net* net);
+sm_status net_upload(sm_net* net);
+sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma);
+
+// Kernel launchers (one per .cu file).
+sm_status launch_rates(const sm_net* net, int64_t C, const double* T, const double* nH,
+                       const double* Av, double zeta, double* k, int64_t ld, cudaStream_t s);
+sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double* y,
+                     double* f, int64_t ld, double* scratch, int64_t ld_scratch, cudaStream_t s);
+sm_status launch_jac(const sm_net* net, int64_t C, const double* k, const double* y,
+                     double* J, int64_t ld, cudaStream_t s);
+
+inline bool ld_ok(int64_t C, int64_t ld) { return C >= 0 && ld >= C && ld % 32 == 0; }
