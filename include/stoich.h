@@ -162,6 +162,108 @@ sm_status sm_rhs_eval(const sm_net* net, int64_t C, const double* d_k, const dou
 sm_status sm_jac_eval(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
                       double* d_J, int64_t ld, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Stiff integration (the role of DLSODES in Section 3): a variable-step,
+ * variable-order (1..5) BDF method with simplified Newton iterations, run
+ * independently for every cell.  The method, step-size / order rules and
+ * Jacobian-refresh policy are fixed (see the option fields):
+ *  - order-q BDF on the last q solution points with Lagrange coefficients,
+ *    degree-q Lagrange predictor (y0 + h f(y0) on the first step);
+ *  - Newton matrix M = I - gamma J (gamma = h / alpha_0), J evaluated at the
+ *    predicted state, refreshed at the first attempt, after j_age_max steps,
+ *    when gamma moved by more than gamma_tol relative, and after a Newton
+ *    failure that used an older J; corrections scaled by 2/(1+gamma/gamma_J);
+ *  - convergence when |delta|_wrms * min(1, rate) <= newton_tol (rate =
+ *    max(0.3 rate, |delta_m|/|delta_m-1|)), at most newton_max iterations;
+ *  - error estimate h/(t_{n+1}-t_{n-q}) |y - y_pred|_wrms, step factor
+ *    0.9 err^(-1/(q+1)) clipped to [0.2, eta_max] (1 after a rejection),
+ *    factors in [1, eta_keep) ignored; neighbouring orders rated after q+1
+ *    steps at order q.  |v|_wrms = sqrt(mean((v_i/(rtol|y_i|+atol))^2)).
+ * The Newton matrix is factorised without pivoting in a minimum-degree order
+ * (as DLSODES's sparse solver does); SM_PREC_FP64 factorises and solves in
+ * FP64, SM_PREC_MIXED in FP32 on the WRMS-equilibrated matrix W M W^-1
+ * while the residual, Jacobian and all state stay FP64.
+ * ------------------------------------------------------------------------ */
+enum { SM_PREC_FP64 = 0, SM_PREC_MIXED = 1 };
+
+typedef struct {
+    double rtol, atol;        /* error weights 1/(rtol |y| + atol)                 */
+    double gamma_tol;         /* refactor when |gamma/gamma_J - 1| > gamma_tol     */
+    double newton_tol;        /* Newton convergence threshold (WRMS units)         */
+    double eta_max;           /* largest step growth factor                        */
+    double eta_keep;          /* growth factors in [1, eta_keep) are not applied   */
+    int32_t q_max;            /* highest BDF order, 1..5                           */
+    int32_t max_steps;        /* accepted steps per cell before SM_CELL_MAXSTEPS   */
+    int32_t j_age_max;        /* accepted steps between Jacobian refreshes         */
+    int32_t newton_max;       /* Newton iterations per attempt, 1..8               */
+    int32_t max_conv_fails;   /* consecutive Newton failures before SM_CELL_CONV   */
+    int32_t precision;        /* SM_PREC_FP64 or SM_PREC_MIXED                     */
+    int32_t use_graph;        /* capture the attempt loop in a CUDA graph (1) or not */
+    int32_t attempts_per_sync;/* attempts launched between completion checks      */
+    int32_t timing_kind;      /* SM_TIME_*: kernel class timed with CUDA events    */
+} sm_opts;
+
+/* Kernel classes of the integrator whose launches sm_state_timing reports. */
+enum { SM_TIME_NONE = 0, SM_TIME_REFRESH = 1, SM_TIME_RHS = 2, SM_TIME_SOLVE = 3,
+       SM_TIME_PREDICT = 4, SM_TIME_FINISH = 5 };
+
+/* Per-cell result of sm_integrate (device array of C entries). */
+typedef struct {
+    int32_t status;        /* SM_CELL_*                                      */
+    int32_t steps;         /* accepted steps                                 */
+    int32_t rejects;       /* error-test failures                            */
+    int32_t conv_fails;    /* Newton convergence failures                    */
+    int32_t newton_iters;  /* Newton iterations (RHS evaluations after init) */
+    int32_t jac_evals;     /* Jacobian evaluations = factorisations          */
+    int32_t q_last;        /* order at the end                               */
+    int32_t pad;
+    double t;              /* time reached                                   */
+    double h;              /* next step size                                 */
+} sm_cell_stats;
+
+typedef struct sm_state sm_state;
+
+/* Defaults: rtol 1e-6, atol 1e-20, gamma_tol 0.3, newton_tol 0.1, eta_max 5,
+ * eta_keep 1.5, q_max 5, max_steps 100000, j_age_max 20, newton_max 4,
+ * max_conv_fails 10, FP64, graph on, 8 attempts per completion check. */
+void sm_opts_default(sm_opts* o);
+
+/* Integrator workspace for up to C cells of `net` (library-owned device
+ * memory: history, Newton vectors and one factorised Newton matrix per cell,
+ * n_s^2 values in the chosen precision).  SM_ENOMEM if it does not fit. */
+sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_state** out);
+sm_status sm_state_free(sm_state* st);
+/* Bytes of device memory the state holds. */
+sm_status sm_state_bytes(const sm_state* st, size_t* bytes);
+
+/* Integrate C cells (C <= the state's capacity) from t = 0 to t_end (s):
+ * d_k = k'[n_r][ld] rate coefficients, d_y = x[n_s][ld] initial abundances,
+ * overwritten with the abundances at t_end (or where a cell stopped).
+ * d_stats (device, C entries, may be NULL) receives per-cell results.
+ * Returns SM_EPARTIAL if any cell did not reach t_end. */
+sm_status sm_integrate(sm_state* st, int64_t C, const double* d_k, double* d_y, int64_t ld,
+                       double t_end, sm_cell_stats* d_stats, void* stream);
+
+/* Stepwise use: sm_state_init sets t = 0 from d_y; each sm_step_bdf call runs
+ * `attempts` BDF attempts (predict, Newton, error test) for every unfinished
+ * cell toward t_end; sm_state_read copies the current solution to d_y and the
+ * per-cell results to d_stats (either may be NULL) and reports how many cells
+ * are still running in *h_running (host, may be NULL; synchronises). */
+sm_status sm_state_init(sm_state* st, int64_t C, const double* d_k, const double* d_y, int64_t ld,
+                        double t_end, void* stream);
+sm_status sm_step_bdf(sm_state* st, const double* d_k, int64_t ld, int32_t attempts, void* stream);
+sm_status sm_state_read(sm_state* st, double* d_y, int64_t ld, sm_cell_stats* d_stats,
+                        int64_t* h_running, void* stream);
+
+/* Instrumentation: *launches = kernels the state has launched so far, and,
+ * when opts.timing_kind selects a class, *ms = summed CUDA-event durations of
+ * that class's launches (*timed = how many were timed; the RHS class times
+ * the rate + gather pair of each Newton round as one launch).  Events are
+ * recorded on the state's stream, inside the captured graph when graphs are
+ * used; sm_state_timing_reset zeroes the totals.  Any pointer may be NULL. */
+sm_status sm_state_timing(const sm_state* st, int64_t* launches, double* ms, int64_t* timed);
+sm_status sm_state_timing_reset(sm_state* st);
+
 /* Wait for all work on `stream` and report (and clear) any error a kernel of
  * this network wrote to its device status word. */
 sm_status sm_sync(const sm_net* net, void* stream);

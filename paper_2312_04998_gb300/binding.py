@@ -46,6 +46,23 @@ class NetInfo_c(ct.Structure):
                 ("rhs_flops", ct.c_double), ("jac_bytes", ct.c_double), ("jac_flops", ct.c_double)]
 
 
+class Opts_c(ct.Structure):
+    _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("gamma_tol", ct.c_double),
+                ("newton_tol", ct.c_double), ("eta_max", ct.c_double), ("eta_keep", ct.c_double),
+                ("q_max", ct.c_int32), ("max_steps", ct.c_int32), ("j_age_max", ct.c_int32),
+                ("newton_max", ct.c_int32), ("max_conv_fails", ct.c_int32), ("precision", ct.c_int32),
+                ("use_graph", ct.c_int32), ("attempts_per_sync", ct.c_int32),
+                ("timing_kind", ct.c_int32)]
+
+
+CELL_STATS_DTYPE = np.dtype([("status", np.int32), ("steps", np.int32), ("rejects", np.int32),
+                             ("conv_fails", np.int32), ("newton_iters", np.int32),
+                             ("jac_evals", np.int32), ("q_last", np.int32), ("pad", np.int32),
+                             ("t", np.float64), ("h", np.float64)])
+PREC = {"fp64": 0, "mixed": 1}
+TIME = {"none": 0, "refresh": 1, "rhs": 2, "solve": 3, "predict": 4, "finish": 5}
+CELL_OK, CELL_MAXSTEPS, CELL_HMIN, CELL_CONV, CELL_NAN, CELL_RUNNING = range(6)
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point.
@@ -64,6 +81,20 @@ _SIGS = [
     ("sm_jac_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_int64, ct.c_void_p]),
     ("sm_sync", ct.c_int32, [ct.c_void_p, ct.c_void_p]),
+    ("sm_opts_default", None, [ct.POINTER(Opts_c)]),
+    ("sm_state_create", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.POINTER(Opts_c), ct.POINTER(ct.c_void_p)]),
+    ("sm_state_free", ct.c_int32, [ct.c_void_p]),
+    ("sm_state_bytes", ct.c_int32, [ct.c_void_p, ct.POINTER(ct.c_size_t)]),
+    ("sm_integrate", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_int64,
+                                  ct.c_double, ct.c_void_p, ct.c_void_p]),
+    ("sm_state_init", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_int64,
+                                   ct.c_double, ct.c_void_p]),
+    ("sm_state_timing", ct.c_int32, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double),
+                                     ct.POINTER(ct.c_int64)]),
+    ("sm_state_timing_reset", ct.c_int32, [ct.c_void_p]),
+    ("sm_step_bdf", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p]),
+    ("sm_state_read", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p,
+                                   ct.POINTER(ct.c_int64), ct.c_void_p]),
 ]
 
 
@@ -193,3 +224,94 @@ class Network:
     def sync(self):
         import torch
         _check(lib().sm_sync(self.h, _stream(torch.device("cuda", self.device))), "sm_sync")
+
+
+def default_opts(**kw) -> Opts_c:
+    o = Opts_c()
+    lib().sm_opts_default(ct.byref(o))
+    for key, v in kw.items():
+        if key == "precision" and isinstance(v, str):
+            v = PREC[v]
+        if key == "timing_kind" and isinstance(v, str):
+            v = TIME[v]
+        setattr(o, key, v)
+    return o
+
+
+class State:
+    """Integrator workspace (sm_state) for up to `cells` cells of `net`."""
+
+    def __init__(self, net: Network, cells: int, **opts):
+        self.net = net
+        self.opts = default_opts(**opts)
+        h = ct.c_void_p()
+        _check(lib().sm_state_create(net.h, int(cells), ct.byref(self.opts), ct.byref(h)),
+               "sm_state_create")
+        self.h = h
+        self.cells = cells
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sm_state_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def timing(self):
+        """(kernel launches so far, summed ms of the timed class, timed launches)."""
+        n, ms, t = ct.c_int64(), ct.c_double(), ct.c_int64()
+        _check(lib().sm_state_timing(self.h, ct.byref(n), ct.byref(ms), ct.byref(t)), "sm_state_timing")
+        return n.value, ms.value, t.value
+
+    def timing_reset(self):
+        _check(lib().sm_state_timing_reset(self.h), "sm_state_timing_reset")
+
+    def nbytes(self) -> int:
+        n = ct.c_size_t()
+        _check(lib().sm_state_bytes(self.h, ct.byref(n)), "sm_state_bytes")
+        return n.value
+
+    def integrate(self, k, y, t_end, C=None, stats=None, allow_partial=True):
+        """Integrate C cells from t = 0 to t_end; y (device [n_s][ld]) is
+        overwritten.  stats: optional device uint8 tensor of C*48 bytes.
+        Returns the status code (SM_OK or SM_EPARTIAL)."""
+        C = y.shape[1] if C is None else C
+        ld = self.net._ld(k, y)
+        code = lib().sm_integrate(self.h, int(C), _dptr(k), _dptr(y), int(ld), float(t_end),
+                                  _dptr(stats) if stats is not None else None, _stream(y.device))
+        if code == SM_EPARTIAL and allow_partial:
+            return code
+        _check(code, "sm_integrate")
+        return code
+
+    def init(self, k, y, t_end, C=None):
+        C = y.shape[1] if C is None else C
+        _check(lib().sm_state_init(self.h, int(C), _dptr(k), _dptr(y), int(self.net._ld(k, y)),
+                                   float(t_end), _stream(y.device)), "sm_state_init")
+
+    def step(self, k, attempts):
+        _check(lib().sm_step_bdf(self.h, _dptr(k), int(k.stride(0)), int(attempts), _stream(k.device)),
+               "sm_step_bdf")
+
+    def read(self, y=None, stats=None):
+        running = ct.c_int64()
+        import torch
+        dev = y.device if y is not None else torch.device("cuda", self.net.device)
+        _check(lib().sm_state_read(self.h, _dptr(y) if y is not None else None,
+                                   int(y.stride(0)) if y is not None else 32,
+                                   _dptr(stats) if stats is not None else None, ct.byref(running),
+                                   _stream(dev)), "sm_state_read")
+        return running.value
+
+
+def stats_tensor(C, device):
+    import torch
+    return torch.zeros(C * CELL_STATS_DTYPE.itemsize, dtype=torch.uint8, device=device)
+
+
+def stats_to_numpy(t):
+    return np.frombuffer(t.cpu().numpy().tobytes(), dtype=CELL_STATS_DTYPE)

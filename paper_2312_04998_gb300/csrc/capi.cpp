@@ -65,7 +65,14 @@ void release_all(sm_net* net) {
   f.d_packed.release();
   f.d_aux.release();
   f.d_chunk.release();
+  Format& g = net->integ;
+  g.d_ptr.release();
+  g.d_packed.release();
+  g.d_aux.release();
+  g.d_chunk.release();
   LUSymbolic& lu = net->lu;
+  lu.d_lrptr.release();
+  lu.d_lridx.release();
   lu.d_lptr.release();
   lu.d_lidx.release();
   lu.d_uptr.release();

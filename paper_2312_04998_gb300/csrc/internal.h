@@ -66,9 +66,10 @@ struct LUSymbolic {
   std::vector<int32_t> perm, iperm;       // perm[p] = species at position p
   std::vector<int32_t> lptr, lidx;        // per pivot: rows below it (positions)
   std::vector<int32_t> uptr, uidx;        // per pivot: columns right of it
+  std::vector<int32_t> lrptr, lridx;      // per row: columns of L left of the diagonal
   std::vector<int32_t> jpos;              // per J pattern entry: dense offset p*ld+q
   int64_t nnz = 0, flops = 0;
-  DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_jpos, d_perm, d_iperm;
+  DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_jpos, d_perm, d_iperm;
 };
 
 struct sm_net {
@@ -84,6 +85,7 @@ struct sm_net {
   // Row orders and column orders for SM_ORDER_NONE / NNZ / RCM.
   std::vector<int32_t> row_order[3], col_order[3];
   Format cur;
+  Format integ;  // CRS in the original order, used inside the integrator
   // Jacobian pattern (CRS, species order) and contribution list per entry:
   // term = coef * k'[j] * (partner >= 0 ? y[partner] : 1).
   std::vector<int32_t> jp_ptr, jp_col, jt_ptr, jt_rx, jt_partner;
@@ -104,12 +106,19 @@ struct sm_net {
 sm_status net_build_host(const sm_net_desc* d, sm_net* net);
 sm_status net_upload(sm_net* net);
 sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma);
+sm_status build_format(const sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma,
+                       Format* out);
 
 // Kernel launchers (one per .cu file).
 sm_status launch_rates(const sm_net* net, int64_t C, const double* T, const double* nH,
                        const double* Av, double zeta, double* k, int64_t ld, cudaStream_t s);
 sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double* y,
                      double* f, int64_t ld, double* scratch, int64_t ld_scratch, cudaStream_t s);
+// Masked CRS right-hand side for the integrator: cells whose mask word has
+// `bit` set are evaluated; whole thread blocks without such a cell exit.
+sm_status launch_rhs_masked(const sm_net* net, int64_t C, const double* k, int64_t ldk,
+                            const double* y, double* f, int64_t ld, double* scratch, int64_t ldr,
+                            const int* mask, int bit, cudaStream_t s);
 sm_status launch_jac(const sm_net* net, int64_t C, const double* k, const double* y,
                      double* J, int64_t ld, cudaStream_t s);
 

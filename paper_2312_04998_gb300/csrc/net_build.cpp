@@ -253,6 +253,18 @@ void build_lu_symbolic(sm_net& net) {
     lu.flops += (int64_t)L.size() + 2 * (int64_t)L.size() * (int64_t)U.size();
   }
   lu.nnz = n + (int64_t)lu.lidx.size() + (int64_t)lu.uidx.size();
+  // row-wise view of L (for row-oriented forward substitution)
+  {
+    std::vector<std::vector<int32_t>> rows(n);
+    for (int32_t k = 0; k < n; ++k)
+      for (int32_t p = lu.lptr[k]; p < lu.lptr[k + 1]; ++p) rows[lu.lidx[p]].push_back(k);
+    lu.lrptr.assign(1, 0);
+    lu.lridx.clear();
+    for (int32_t i = 0; i < n; ++i) {
+      lu.lridx.insert(lu.lridx.end(), rows[i].begin(), rows[i].end());
+      lu.lrptr.push_back((int32_t)lu.lridx.size());
+    }
+  }
   // head: first pivot from which the trailing block is at least 90 % filled
   lu.head = n;
   for (int32_t k = 0; k < n; ++k) {
@@ -383,7 +395,8 @@ inline uint32_t pack(int32_t index, int32_t coef) {
 
 }  // namespace
 
-sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma) {
+sm_status build_format(const sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma,
+                       Format* out) {
   if (fmt < SM_FMT_CRS || fmt > SM_FMT_SELL || order < SM_ORDER_NONE || order > SM_ORDER_RCM)
     return SM_EINVAL;
   if (fmt == SM_FMT_SELL && (C < 1 || C > 32 || sigma < 1)) return SM_EINVAL;
@@ -486,18 +499,13 @@ sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, 
     const int32_t n_chunks = 32;  // must match the CRS kernel's chunks per CTA
     for (int32_t c = 0; c <= n_chunks; ++c) f.chunk_nz.push_back((int32_t)((int64_t)nnz * c / n_chunks));
   }
-  net->info.fmt = fmt;
-  net->info.order = order;
-  net->info.sell_C = f.C;
-  net->info.sell_sigma = f.sigma;
-  net->info.fmt_entries = (int64_t)f.idx.size();
   // upload (skipped for host-only networks, device < 0)
-  net->cur.d_ptr.release();
-  net->cur.d_packed.release();
-  net->cur.d_aux.release();
-  net->cur.d_chunk.release();
-  net->cur = std::move(f);
-  Format& g = net->cur;
+  out->d_ptr.release();
+  out->d_packed.release();
+  out->d_aux.release();
+  out->d_chunk.release();
+  *out = std::move(f);
+  Format& g = *out;
   if (net->device < 0) return SM_OK;
   sm_status st;
   if (!g.ptr.empty() && (st = g.d_ptr.upload(g.ptr.data(), g.ptr.size() * 4)) != SM_OK) return st;
@@ -505,6 +513,17 @@ sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, 
   if (!g.aux.empty() && (st = g.d_aux.upload(g.aux.data(), g.aux.size() * 4)) != SM_OK) return st;
   if (!g.chunk_nz.empty() && (st = g.d_chunk.upload(g.chunk_nz.data(), g.chunk_nz.size() * 4)) != SM_OK)
     return st;
+  return SM_OK;
+}
+
+sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma) {
+  sm_status st = build_format(net, fmt, order, C, sigma, &net->cur);
+  if (st != SM_OK) return st;
+  net->info.fmt = net->cur.fmt;
+  net->info.order = net->cur.order;
+  net->info.sell_C = net->cur.C;
+  net->info.sell_sigma = net->cur.sigma;
+  net->info.fmt_entries = (int64_t)net->cur.idx.size();
   return SM_OK;
 }
 
@@ -554,10 +573,12 @@ sm_status net_upload(sm_net* net) {
   if (!lu.lidx.empty() && (st = lu.d_lidx.upload(lu.lidx.data(), lu.lidx.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_uptr.upload(lu.uptr.data(), lu.uptr.size() * 4)) != SM_OK) return st;
   if (!lu.uidx.empty() && (st = lu.d_uidx.upload(lu.uidx.data(), lu.uidx.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_lrptr.upload(lu.lrptr.data(), lu.lrptr.size() * 4)) != SM_OK) return st;
+  if (!lu.lridx.empty() && (st = lu.d_lridx.upload(lu.lridx.data(), lu.lridx.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_jpos.upload(lu.jpos.data(), lu.jpos.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_perm.upload(lu.perm.data(), lu.perm.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_iperm.upload(lu.iperm.data(), lu.iperm.size() * 4)) != SM_OK) return st;
   int32_t zero = 0;
   if ((st = net->d_status.upload(&zero, 4)) != SM_OK) return st;
-  return SM_OK;
+  return build_format(net, SM_FMT_CRS, SM_ORDER_NONE, 1, 1, &net->integ);
 }
