@@ -30,7 +30,7 @@ enum : int {
 };
 
 struct Dev {
-  int n, n_r, nnz_j, mixed;
+  int n, n_r, nnz_j, mixed, head;
   int64_t C, ld;
   double rtol, atol, gamma_tol, newton_tol, eta_max, eta_keep, t_end;
   int q_max, max_steps, j_age_max, newton_max, max_conv_fails;
@@ -207,20 +207,52 @@ __global__ void predict_kernel(Dev d) {
 }
 
 // ---------------------------------------------------------------------------
-// refresh: J, M = I - gamma J and its LU (in place, dense storage, sparse
-// elimination schedule).  One CTA per listed cell, grid-stride over the list.
+// refresh: J, M = I - gamma J and its LU without pivoting, in place in dense
+// per-cell storage (elimination order = minimum degree).  One CTA per cell on
+// the compacted refresh list (grid-stride).  The first `head` pivots are
+// sparse and follow the symbolic schedule; the trailing block from `head` on
+// is >= 90 % dense and is factorised by a right-looking blocked algorithm:
+// panels of kNB columns are factorised in shared memory, U12 is solved in
+// shared memory, and the trailing update A22 -= L21 U12 runs as a register-
+// tiled GEMM (kTM x kTN outputs per thread).  Inverse pivots replace the
+// diagonal.
 // ---------------------------------------------------------------------------
+constexpr int kRefreshThreads = 256;
+constexpr int kNB = 32;
+constexpr int kTM = 4, kTN = 4;
+
+size_t refresh_smem_bytes(int n, int head, size_t esz) {
+  const size_t nt = (size_t)(n - head);
+  return esz * (nt * (kNB + 1) + (size_t)kNB * nt);
+}
+
 template <class T>
-__global__ void __launch_bounds__(512) refresh_kernel(Dev d, const double* __restrict__ k, int64_t ldk) {
+__global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(Dev d, const double* __restrict__ k,
+                                                                 int64_t ldk) {
+  extern __shared__ unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  const int n = d.n, ldm = d.ldm;
+  const int n = d.n, ldm = d.ldm, h = d.head, nt = n - h;
+  T* P = reinterpret_cast<T*>(smem_raw);            // panel, pitch kNB + 1
+  T* U = P + (size_t)nt * (kNB + 1);                // U12 block, pitch r
+  constexpr int PP = kNB + 1;
   const int count = d.counters[0];
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t c = d.list[e];
     T* A = static_cast<T*>(d.lu) + c * d.lu_stride;
     const double gamma = d.gam[c];
-    for (int64_t i = tid; i < (int64_t)n * ldm; i += nthr) A[i] = T(0);
+    // zero the dense trailing block and the head's pattern entries
+    for (int64_t i = tid; i < (int64_t)nt * nt; i += nthr) {
+      const int r = (int)(i / nt), q = (int)(i - (int64_t)r * nt);
+      A[(int64_t)(h + r) * ldm + h + q] = T(0);
+    }
+    for (int kp = warp; kp < h; kp += nwarps) {
+      for (int p = __ldg(d.lptr + kp) + lane; p < __ldg(d.lptr + kp + 1); p += 32)
+        A[(int64_t)__ldg(d.lidx + p) * ldm + kp] = T(0);
+      for (int p = __ldg(d.uptr + kp) + lane; p < __ldg(d.uptr + kp + 1); p += 32)
+        A[(int64_t)kp * ldm + __ldg(d.uidx + p)] = T(0);
+      if (lane == 0) A[(int64_t)kp * ldm + kp] = T(0);
+    }
     if (d.mixed)
       for (int s = tid; s < n; s += nthr) V(d.wf, d, s, c) = V(d.w, d, s, c);
     __syncthreads();
@@ -244,7 +276,8 @@ __global__ void __launch_bounds__(512) refresh_kernel(Dev d, const double* __res
       A[pos] = T(m);
     }
     __syncthreads();
-    for (int kp = 0; kp < n; ++kp) {
+    // sparse head pivots
+    for (int kp = 0; kp < h; ++kp) {
       const T inv = T(1) / A[(int64_t)kp * ldm + kp];
       const int l0 = __ldg(d.lptr + kp), l1 = __ldg(d.lptr + kp + 1);
       for (int p = l0 + tid; p < l1; p += nthr) A[(int64_t)__ldg(d.lidx + p) * ldm + kp] *= inv;
@@ -259,6 +292,80 @@ __global__ void __launch_bounds__(512) refresh_kernel(Dev d, const double* __res
           const int j = __ldg(d.uidx + u0 + b);
           Ai[j] -= l * Ak[j];
         }
+      }
+      __syncthreads();
+    }
+    // dense trailing block: blocked right-looking LU
+    for (int p0 = h; p0 < n; p0 += kNB) {
+      const int w = min(kNB, n - p0), m = n - p0, r = m - w;
+      for (int i = tid; i < m * w; i += nthr) {
+        const int a = i / w, b = i - a * w;
+        P[a * PP + b] = A[(int64_t)(p0 + a) * ldm + p0 + b];
+      }
+      __syncthreads();
+      for (int kk = 0; kk < w; ++kk) {
+        const T inv = T(1) / P[kk * PP + kk];
+        for (int i = kk + 1 + tid; i < m; i += nthr) P[i * PP + kk] *= inv;
+        __syncthreads();
+        const int cols = w - kk - 1;
+        if (cols > 0)
+          for (int i = tid; i < (m - kk - 1) * cols; i += nthr) {
+            const int a = kk + 1 + i / cols, b = kk + 1 + i % cols;
+            P[a * PP + b] -= P[a * PP + kk] * P[kk * PP + b];
+          }
+        if (tid == 0) P[kk * PP + kk] = inv;
+        __syncthreads();
+      }
+      for (int i = tid; i < m * w; i += nthr) {
+        const int a = i / w, b = i - a * w;
+        A[(int64_t)(p0 + a) * ldm + p0 + b] = P[a * PP + b];
+      }
+      if (r > 0) {
+        // U12 = L11^-1 A12, one thread per column
+        for (int i = tid; i < w * r; i += nthr) {
+          const int a = i / r, b = i - a * r;
+          U[a * r + b] = A[(int64_t)(p0 + a) * ldm + p0 + w + b];
+        }
+        __syncthreads();
+        for (int b = tid; b < r; b += nthr) {
+          for (int kk = 0; kk < w; ++kk) {
+            const T u = U[kk * r + b];
+            for (int a = kk + 1; a < w; ++a) U[a * r + b] -= P[a * PP + kk] * u;
+          }
+          for (int a = 0; a < w; ++a) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * r + b];
+        }
+        __syncthreads();
+        // A22 -= L21 U12, tiles of (16 kTM) x (16 kTN)
+        const int ty = tid / 16, tx = tid % 16;
+        constexpr int BM = 16 * kTM, BN = 16 * kTN;
+        for (int t0 = 0; t0 < r; t0 += BM)
+          for (int u0 = 0; u0 < r; u0 += BN) {
+            T acc[kTM][kTN];
+            const int i0 = t0 + ty * kTM, j0 = u0 + tx * kTN;
+#pragma unroll
+            for (int a = 0; a < kTM; ++a)
+#pragma unroll
+              for (int b = 0; b < kTN; ++b)
+                acc[a][b] = (i0 + a < r && j0 + b < r)
+                                ? A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] : T(0);
+            for (int kk = 0; kk < w; ++kk) {
+              T lv[kTM], uv[kTN];
+#pragma unroll
+              for (int a = 0; a < kTM; ++a) lv[a] = (i0 + a < r) ? P[(w + i0 + a) * PP + kk] : T(0);
+#pragma unroll
+              for (int b = 0; b < kTN; ++b) uv[b] = (j0 + b < r) ? U[kk * r + j0 + b] : T(0);
+#pragma unroll
+              for (int a = 0; a < kTM; ++a)
+#pragma unroll
+                for (int b = 0; b < kTN; ++b) acc[a][b] -= lv[a] * uv[b];
+            }
+#pragma unroll
+            for (int a = 0; a < kTM; ++a)
+#pragma unroll
+              for (int b = 0; b < kTN; ++b)
+                if (i0 + a < r && j0 + b < r)
+                  A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] = acc[a][b];
+          }
       }
       __syncthreads();
     }
@@ -660,7 +767,8 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   predict_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_PREDICT, false, s)) != SM_OK) return r;
   if ((r = time_mark(st, SM_TIME_REFRESH, true, s)) != SM_OK) return r;
-  refresh_kernel<T><<<st->refresh_ctas, 512, 0, s>>>(d, k, ldk);
+  refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, refresh_smem_bytes(d.n, d.head, sizeof(T)), s>>>(
+      d, k, ldk);
   if ((r = time_mark(st, SM_TIME_REFRESH, false, s)) != SM_OK) return r;
   const size_t smem = sizeof(T) * (size_t)kSolveWarps * d.n;
   for (int m = 0; m < d.newton_max; ++m) {
@@ -814,6 +922,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.newton_max = o.newton_max;
   d.max_conv_fails = o.max_conv_fails;
   d.ldm = lu.ld;
+  d.head = lu.head;
   sm_status r = SM_OK;
   auto fail = [&](sm_status e) {
     free_state(st);
@@ -859,7 +968,22 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   if (cudaMallocHost(&st->h_counters, 4 * sizeof(int)) != cudaSuccess) return fail(SM_ENOMEM);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device);
-  st->refresh_ctas = 2 * (sms > 0 ? sms : 1);
+  const size_t rsm = refresh_smem_bytes(n, lu.head, esz);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device);
+  if ((int64_t)rsm > smem_max) return fail(SM_ENOTSUP);
+  if (d.mixed) {
+    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+  } else {
+    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+  }
+  int per_sm = 0;
+  if (d.mixed) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<float>, kRefreshThreads, rsm);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<double>, kRefreshThreads, rsm);
+  }
+  st->refresh_ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   SM_TRY_CUDA(cudaMemset(st->scal_i.p, 0, st->scal_i.bytes));
   *out = st;
   return SM_OK;

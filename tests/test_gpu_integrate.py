@@ -83,11 +83,11 @@ def test_worked_example_riccati(torch, B, precision):
     assert np.allclose(y[0] + 2 * y[1], 1.0, rtol=1e-13)
 
 
-def load_truth(name):
+def load_truth(name, key="y"):
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", f"integrate_truth_{name}.json")) as fh:
-        return np.array(json.load(fh)["y"]).T
+        return np.array(json.load(fh)[key]).T
 
 
 def weighted_err(y, ref, rtol=1e-6, atol=1e-20):
@@ -167,3 +167,22 @@ def test_max_steps_reported(torch, B):
     y, stats, code = run_gpu(torch, B, d, k, y0, 1e6 * YEAR, max_steps=5)
     assert code == B.SM_EPARTIAL
     assert np.all(stats["status"] == B.CELL_MAXSTEPS) and np.all(stats["steps"] == 5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_network_matches_oracle(torch, B, precision):
+    """4 cells of the 470 x 6000 network to 1e6 yr against the stored
+    rtol-1e-10 truth; the bar is the oracle's own rtol-1e-6 distance to it
+    (stored by the same script), doubled for FP64 and quadrupled for mixed."""
+    from tests.golden.make_integrate_truth import case_inputs
+    d, k, y0, t_end = case_inputs("large")
+    truth = load_truth("large")
+    yo = load_truth("large", "y_rtol6")
+    y, stats, code = run_gpu(torch, B, d, k, y0, t_end, precision=precision)
+    assert code == B.SM_OK, stats["status"]
+    e_o = weighted_err(yo, truth)
+    e_g = weighted_err(y, truth)
+    factor = 2.0 if precision == "fp64" else 4.0
+    assert e_g <= factor * max(e_o, 1.0), (e_g, e_o)
+    E = on.element_matrix(d).astype(float)
+    assert np.allclose(E[:3] @ y, E[:3] @ y0, rtol=1e-12)
