@@ -42,7 +42,8 @@ enum {
     SM_ENOTCONS = 4,   /* network does not conserve elements / charge (E.S!=0)  */
     SM_ETIMEOUT = 5,   /* a bounded device wait ran out                         */
     SM_EPARTIAL = 6,   /* the call completed but some cells failed (see stats)  */
-    SM_ENOTSUP = 7     /* combination not supported                             */
+    SM_ENOTSUP = 7,    /* combination not supported                             */
+    SM_ETOOBIG = 8     /* request exceeds a fixed-size internal buffer          */
 };
 
 /* Per-cell integration status (sm_cell_stats.status). */
@@ -156,6 +157,26 @@ sm_status sm_rates_eval(const sm_net* net, int64_t C, const double* d_T, const d
  * sm_net_set_format.  d_f must not alias d_k or d_y. */
 sm_status sm_rhs_eval(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
                       double* d_f, int64_t ld, void* stream);
+
+/* Right-hand side without any device allocation.  Same inputs, outputs,
+ * formats and results as sm_rhs_eval, for callers that cannot allow a library
+ * to call cudaMalloc: code that runs while a stream is being captured into a
+ * CUDA graph (allocation is not permitted there), and host codes that reserve
+ * the device memory up front for their own pool.  The per-reaction rate
+ * buffer lives in one fixed array compiled into the library
+ * (SM_STATIC_SCRATCH_DOUBLES doubles, 32 MiB, held by every GPU that loads
+ * the library until the process exits); requests with
+ * n_r * round_up(C, 32) > SM_STATIC_SCRATCH_DOUBLES return SM_ETOOBIG.
+ * The first call on a device looks up that array's device address (and loads
+ * the coefficient table), so make it once before any stream capture.  Every
+ * call on a device shares the array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The array keeps the last call's contents; nothing in it needs to start at
+ * zero because each call writes every value it reads.
+ * The paper has no counterpart to this entry point. */
+#define SM_STATIC_SCRATCH_DOUBLES 4194304
+sm_status sm_rhs_eval_static(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
+                             double* d_f, int64_t ld, void* stream);
 
 /* Jacobian values J = S dR/dx on the static pattern (SM_X_JPAT_*): d_J is
  * [nnz_J][ld], entry p of the pattern for cell c at p*ld + c, FP64. */

@@ -16,7 +16,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libstoich.so")
 
-SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ENOTCONS, SM_ETIMEOUT, SM_EPARTIAL, SM_ENOTSUP = range(8)
+SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ENOTCONS, SM_ETIMEOUT, SM_EPARTIAL, SM_ENOTSUP, SM_ETOOBIG = range(9)
+STATIC_SCRATCH_DOUBLES = 4194304
 FMT = {"crs": 0, "coo": 1, "ccs": 2, "sell": 3}
 ORDER = {"none": 0, "nnz": 1, "rcm": 2}
 X_ROW_ORDER, X_COL_ORDER, X_FMT_PTR, X_FMT_IDX, X_FMT_IDX2, X_FMT_VAL, X_FMT_LEN, \
@@ -78,6 +79,8 @@ _SIGS = [
                                    ct.c_double, ct.c_void_p, ct.c_int64, ct.c_void_p]),
     ("sm_rhs_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_int64, ct.c_void_p]),
+    ("sm_rhs_eval_static", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                        ct.c_int64, ct.c_void_p]),
     ("sm_jac_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_int64, ct.c_void_p]),
     ("sm_sync", ct.c_int32, [ct.c_void_p, ct.c_void_p]),
@@ -213,6 +216,13 @@ class Network:
         ld = self._ld(k, y, f)
         _check(lib().sm_rhs_eval(self.h, int(C), _dptr(k), _dptr(y), _dptr(f), int(ld),
                                  _stream(f.device)), "sm_rhs_eval")
+        return f
+
+    def rhs_eval_static(self, k, y, f, C):
+        """sm_rhs_eval_static: same result as rhs_eval, no device allocation."""
+        ld = self._ld(k, y, f)
+        _check(lib().sm_rhs_eval_static(self.h, int(C), _dptr(k), _dptr(y), _dptr(f), int(ld),
+                                        _stream(f.device)), "sm_rhs_eval_static")
         return f
 
     def jac_eval(self, k, y, J, C):

@@ -106,6 +106,7 @@ const char* sm_status_str(sm_status s) {
     case SM_ETIMEOUT: return "a bounded device wait ran out";
     case SM_EPARTIAL: return "some cells failed; see their status";
     case SM_ENOTSUP: return "not supported";
+    case SM_ETOOBIG: return "request exceeds the fixed-size internal buffer (see SM_STATIC_SCRATCH_DOUBLES)";
     default: return "unknown status";
   }
 }
