@@ -73,6 +73,15 @@ void release_all(sm_net* net) {
   LUSymbolic& lu = net->lu;
   lu.d_lrptr.release();
   lu.d_lridx.release();
+  lu.d_ucptr.release();
+  lu.d_ucidx.release();
+  lu.d_jrc.release();
+  lu.d_uoff.release();
+  lu.d_lrhead.release();
+  lu.d_lrhoff.release();
+  lu.d_u12off.release();
+  lu.d_lrhk.release();
+  net->d_jt_slot.release();
   lu.d_lptr.release();
   lu.d_lidx.release();
   lu.d_uptr.release();

@@ -16,6 +16,7 @@
 //   finish    thread per cell: error test, order / step selection, history.
 // The host enqueues attempts in groups (captured once in a CUDA graph) and
 // reads back only the number of running cells between groups.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -44,8 +45,10 @@ struct Dev {
   void* lu;
   int64_t lu_stride;
   int ldm;
-  const int *perm, *iperm, *lptr, *lidx, *uptr, *uidx, *lrptr, *lridx, *jp_ptr, *jt_ptr, *jpos;
-  const int2* jt_word;
+  const int *perm, *iperm, *lptr, *lidx, *uptr, *uidx, *lrptr, *lridx, *ucptr, *ucidx, *jp_ptr, *jt_ptr,
+      *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk;
+  void* l21_scratch;
+  const int2 *jt_word, *jt_slot, *reac;
 };
 
 __device__ __forceinline__ double& V(double* a, const Dev& d, int s, int64_t c) {
@@ -209,42 +212,93 @@ __global__ void predict_kernel(Dev d) {
 // ---------------------------------------------------------------------------
 // refresh: J, M = I - gamma J and its LU without pivoting, in place in dense
 // per-cell storage (elimination order = minimum degree).  One CTA per cell on
-// the compacted refresh list (grid-stride).  The first `head` pivots are
-// sparse and follow the symbolic schedule; the trailing block from `head` on
-// is >= 90 % dense and is factorised by a right-looking blocked algorithm:
-// panels of kNB columns are factorised in shared memory, U12 is solved in
-// shared memory, and the trailing update A22 -= L21 U12 runs as a register-
-// tiled GEMM (kTM x kTN outputs per thread).  Inverse pivots replace the
-// diagonal.
+// the compacted refresh list (grid-stride).  With M = [A11 A12; A21 A22]
+// split at the first `head` pivots (sparse) and the >= 90 % dense trailing
+// block:
+//  A  dR_j/dx for both reactant slots of every reaction is formed once in
+//     shared memory (FP64) and M is gathered at the Jacobian pattern;
+//  B  A11 is factorised in shared memory by one warp; the rows of
+//     L21 = A21 U11^-1 and the columns of U12 = L11^-1 A12 are solved one
+//     warp each (entries held by lanes, resolved in order with shuffles);
+//  C  the trailing block is factorised right-looking by panels of kNB
+//     columns.  The head's Schur complement -L21 U12 is not applied up front:
+//     each trailing entry receives it when it is loaded into its panel or U
+//     block, the one time it is read before it is final (the additions
+//     commute).  Panel and U12 block live in shared memory; the trailing
+//     update is a register-tiled GEMM.
+// Inverse pivots replace the diagonal.
 // ---------------------------------------------------------------------------
 constexpr int kRefreshThreads = 256;
 constexpr int kNB = 32;
 constexpr int kTM = 4, kTN = 4;
+constexpr int kBM = 16 * kTM, kBN = 16 * kTN;
+constexpr int kHeadG = 4;                 // head entries held per lane
+constexpr int kHeadLanes = 32 * kHeadG;   // longest L21 row / U12 column held in a warp
 
-size_t refresh_smem_bytes(int n, int head, size_t esz) {
-  const size_t nt = (size_t)(n - head);
-  return esz * (nt * (kNB + 1) + (size_t)kNB * nt);
-}
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Shared-memory plan (bytes) shared by host and device.
+struct RefreshPlan {
+  int pitch;          // column pitch of the panel buffer
+  int upitch;         // row pitch of the U block buffer
+  int n_u12;          // staged U12 entries (head rows, tail columns)
+  int n_l21;          // L21 entries (tail rows, head columns)
+  int n_panels;       // 32-wide panels of the trailing block
+  bool head_smem;     // phase B with A11 in shared memory (else pivot by pivot)
+  size_t bytes;
+};
+
+template <class T> struct Vec4;
+template <> struct Vec4<float> {
+  float a[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+  }
+};
+template <> struct Vec4<double> {
+  double a[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 v0 = *reinterpret_cast<const double2*>(p);
+    const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+    a[0] = v0.x; a[1] = v0.y; a[2] = v1.x; a[3] = v1.y;
+  }
+};
+
+template <class T> __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 template <class T>
-__global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(Dev d, const double* __restrict__ k,
-                                                                 int64_t ldk) {
-  extern __shared__ unsigned char smem_raw[];
+__global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, const double* __restrict__ k,
+                                                                 int64_t ldk, RefreshPlan plan) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  const int n = d.n, ldm = d.ldm, h = d.head, nt = n - h;
-  T* P = reinterpret_cast<T*>(smem_raw);            // panel, pitch kNB + 1
-  T* U = P + (size_t)nt * (kNB + 1);                // U12 block, pitch r
-  constexpr int PP = kNB + 1;
+  const int n = d.n, n_r = d.n_r, ldm = d.ldm, h = d.head, nt = n - h, pitch = plan.pitch;
+  const int np1 = plan.n_panels + 1;
+  T* Pt = reinterpret_cast<T*>(smem_raw);           // panel, column-major, kNB columns
+  T* U = Pt + (size_t)kNB * pitch;                  // U12 block, kNB rows, pitch upitch
+  const int upitch = plan.upitch;
+  T* su_val = U + (size_t)kNB * upitch;             // U12 entries of the head rows (phase B on)
+  int* su_off = reinterpret_cast<int*>(su_val + plan.n_u12);
+  unsigned short* su_col = reinterpret_cast<unsigned short*>(su_off + h * np1);
+  double* dR = reinterpret_cast<double*>(smem_raw); // phase A: [n_r][2] (before the U12 stage)
+  float* wsf;
+  float* wif;
+  T* A11 = reinterpret_cast<T*>(smem_raw);          // phase B: h x h (below su_val)
+  double* coef = dR + 2 * n_r;                      // (double)(int8_t)i, J coefficients
+  wsf = reinterpret_cast<float*>(coef + 256);
+  wif = wsf + n;
+  // this CTA's copy of L21 in compact row order (phase B writes, phase C reads)
+  T* l21 = static_cast<T*>(d.l21_scratch) + (size_t)blockIdx.x * plan.n_l21;
   const int count = d.counters[0];
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t c = d.list[e];
     T* A = static_cast<T*>(d.lu) + c * d.lu_stride;
     const double gamma = d.gam[c];
     // zero the dense trailing block and the head's pattern entries
-    for (int64_t i = tid; i < (int64_t)nt * nt; i += nthr) {
-      const int r = (int)(i / nt), q = (int)(i - (int64_t)r * nt);
-      A[(int64_t)(h + r) * ldm + h + q] = T(0);
+    for (int r = warp; r < nt; r += nwarps) {
+      T* row = A + (int64_t)(h + r) * ldm + h;
+      for (int q = lane; q < nt; q += 32) row[q] = T(0);
     }
     for (int kp = warp; kp < h; kp += nwarps) {
       for (int p = __ldg(d.lptr + kp) + lane; p < __ldg(d.lptr + kp + 1); p += 32)
@@ -253,111 +307,319 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(Dev d, const d
         A[(int64_t)kp * ldm + __ldg(d.uidx + p)] = T(0);
       if (lane == 0) A[(int64_t)kp * ldm + kp] = T(0);
     }
+    // ---- phase A
+    for (int i = tid; i < 256; i += nthr) coef[i] = (double)(int8_t)i;
+    for (int j = tid; j < n_r; j += nthr) {
+      const int2 rc = __ldg(d.reac + j);
+      const double kv = k[(int64_t)j * ldk + c];
+      dR[2 * j] = rc.y >= 0 ? kv * d.ypred[(int64_t)rc.y * d.ld + c] : kv;
+      dR[2 * j + 1] = rc.y >= 0 ? kv * d.ypred[(int64_t)rc.x * d.ld + c] : 0.0;
+    }
     if (d.mixed)
-      for (int s = tid; s < n; s += nthr) V(d.wf, d, s, c) = V(d.w, d, s, c);
+      for (int s = tid; s < n; s += nthr) {
+        const double wv = V(d.w, d, s, c);
+        V(d.wf, d, s, c) = wv;
+        wsf[s] = (float)wv;
+        wif[s] = (float)(1.0 / wv);
+      }
     __syncthreads();
-    // M = I - gamma J at the pattern positions (J gathered in FP64)
     for (int p = tid; p < d.nnz_j; p += nthr) {
       double acc = 0.0;
-      const int t1 = __ldg(d.jt_ptr + p + 1);
-      for (int t = __ldg(d.jt_ptr + p); t < t1; ++t) {
-        const int2 wd = __ldg(d.jt_word + t);
-        double v = k[(int64_t)(wd.x & 0xFFFFFF) * ldk + c];
-        if (wd.y >= 0) v *= d.ypred[(int64_t)wd.y * d.ld + c];
-        acc = fma((double)(int8_t)((uint32_t)wd.x >> 24), v, acc);
+      const int t0 = __ldg(d.jt_ptr + p), t1 = __ldg(d.jt_ptr + p + 1);
+      const int rc = __ldg(d.jrc + p);
+      int t = t0;
+      for (; t + 1 < t1; t += 2) {
+        const int2 wa = __ldg(d.jt_slot + t), wb = __ldg(d.jt_slot + t + 1);
+        acc = fma(coef[(uint32_t)wa.x >> 24], dR[2 * (wa.x & 0xFFFFFF) + wa.y], acc);
+        acc = fma(coef[(uint32_t)wb.x >> 24], dR[2 * (wb.x & 0xFFFFFF) + wb.y], acc);
       }
-      const int pos = __ldg(d.jpos + p);
-      const int pi = pos / ldm, pj = pos - pi * ldm;
-      double m = (pi == pj ? 1.0 : 0.0) - gamma * acc;
+      if (t < t1) {
+        const int2 wa = __ldg(d.jt_slot + t);
+        acc = fma(coef[(uint32_t)wa.x >> 24], dR[2 * (wa.x & 0xFFFFFF) + wa.y], acc);
+      }
+      const int pi = rc >> 16, pj = rc & 0xFFFF;
+      const double m = fma(-gamma, acc, pi == pj ? 1.0 : 0.0);
+      T* dst = A + (int64_t)pi * ldm + pj;
       if (d.mixed) {
-        // equilibrated W M W^-1 with the error weights of this step
-        m *= V(d.w, d, __ldg(d.perm + pi), c) / V(d.w, d, __ldg(d.perm + pj), c);
+        // W M W^-1 with the error weights of this step (scaling in FP32)
+        *dst = T((float)m * (wsf[__ldg(d.perm + pi)] * wif[__ldg(d.perm + pj)]));
+      } else {
+        *dst = T(m);
       }
-      A[pos] = T(m);
     }
     __syncthreads();
-    // sparse head pivots
-    for (int kp = 0; kp < h; ++kp) {
-      const T inv = T(1) / A[(int64_t)kp * ldm + kp];
-      const int l0 = __ldg(d.lptr + kp), l1 = __ldg(d.lptr + kp + 1);
-      for (int p = l0 + tid; p < l1; p += nthr) A[(int64_t)__ldg(d.lidx + p) * ldm + kp] *= inv;
+    // ---- phase B: sparse head
+    if (plan.head_smem) {
+      for (int i = tid; i < h * h; i += nthr) A11[i] = T(0);
       __syncthreads();
-      if (tid == 0) A[(int64_t)kp * ldm + kp] = inv;
-      const int u0 = __ldg(d.uptr + kp), nU = __ldg(d.uptr + kp + 1) - u0;
-      const T* Ak = A + (int64_t)kp * ldm;
-      for (int a = l0 + warp; a < l1; a += nwarps) {
-        T* Ai = A + (int64_t)__ldg(d.lidx + a) * ldm;
-        const T l = Ai[kp];
-        for (int b = lane; b < nU; b += 32) {
-          const int j = __ldg(d.uidx + u0 + b);
-          Ai[j] -= l * Ak[j];
+      for (int kp = warp; kp < h; kp += nwarps) {
+        for (int p = __ldg(d.lptr + kp) + lane; p < __ldg(d.lptr + kp + 1); p += 32) {
+          const int i = __ldg(d.lidx + p);
+          if (i < h) A11[i * h + kp] = A[(int64_t)i * ldm + kp];
+        }
+        for (int p = __ldg(d.uptr + kp) + lane; p < __ldg(d.uptr + kp + 1); p += 32) {
+          const int j = __ldg(d.uidx + p);
+          if (j < h) A11[kp * h + j] = A[(int64_t)kp * ldm + j];
+        }
+        if (lane == 0) A11[kp * h + kp] = A[(int64_t)kp * ldm + kp];
+      }
+      __syncthreads();
+      if (warp == 0) {
+        for (int kp = 0; kp < h; ++kp) {
+          const T inv = T(1) / A11[kp * h + kp];
+          const int l0 = __ldg(d.lptr + kp), l1 = __ldg(d.lptr + kp + 1);
+          const int u0 = __ldg(d.uptr + kp), u1 = __ldg(d.uptr + kp + 1);
+          for (int p = l0 + lane; p < l1; p += 32) {
+            const int i = __ldg(d.lidx + p);
+            if (i < h) {
+              const T l = A11[i * h + kp] * inv;
+              A11[i * h + kp] = l;
+              for (int q = u0; q < u1; ++q) {
+                const int j = __ldg(d.uidx + q);
+                if (j >= h) break;
+                A11[i * h + j] -= l * A11[kp * h + j];
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) A11[kp * h + kp] = inv;
+          __syncwarp();
         }
       }
       __syncthreads();
+      for (int r = warp; r < h; r += nwarps)
+        for (int q = lane; q < h; q += 32) A[(int64_t)r * ldm + q] = A11[r * h + q];
+      // L21 rows (warp per row): l_ik = (a_ik - sum_{m<k} l_im u_mk) / u_kk
+      for (int i = h + warp; i < n; i += nwarps) {
+        T* Ai = A + (int64_t)i * ldm;
+        const int p0 = __ldg(d.lrptr + i), cnt = __ldg(d.lrhead + i - h);
+        int kc[kHeadG];
+        T av[kHeadG], acc[kHeadG];
+#pragma unroll
+        for (int g = 0; g < kHeadG; ++g) {
+          const int q = lane + 32 * g;
+          kc[g] = q < cnt ? __ldg(d.lridx + p0 + q) : 0;
+          av[g] = q < cnt ? Ai[kc[g]] : T(0);
+          acc[g] = T(0);
+        }
+        for (int q = 0; q < cnt; ++q) {
+          const int gq = q >> 5, src = q & 31;
+          T mine = T(0), piv = T(0);
+          int kq = 0;
+#pragma unroll
+          for (int g = 0; g < kHeadG; ++g)
+            if (g == gq) {
+              mine = av[g] - acc[g];
+              kq = kc[g];
+            }
+          kq = shfl(kq, src);
+          piv = A11[kq * h + kq];
+          const T lq = shfl(mine, src) * piv;
+#pragma unroll
+          for (int g = 0; g < kHeadG; ++g) {
+            if (g == gq && lane == src) av[g] = lq;
+            const int qq = lane + 32 * g;
+            if (qq > q && qq < cnt) acc[g] += lq * A11[kq * h + kc[g]];
+          }
+        }
+        const int o = __ldg(d.lrhoff + i - h);
+#pragma unroll
+        for (int g = 0; g < kHeadG; ++g)
+          if (lane + 32 * g < cnt) {
+            Ai[kc[g]] = av[g];
+            l21[o + lane + 32 * g] = av[g];
+          }
+      }
+      // U12 columns (warp per column): u_kj = a_kj - sum_{m<k} l_km u_mj
+      for (int j = h + warp; j < n; j += nwarps) {
+        const int q0 = __ldg(d.ucptr + j - h), cnt = __ldg(d.ucptr + j - h + 1) - q0;
+        int kr[kHeadG];
+        T av[kHeadG], acc[kHeadG];
+#pragma unroll
+        for (int g = 0; g < kHeadG; ++g) {
+          const int q = lane + 32 * g;
+          kr[g] = q < cnt ? __ldg(d.ucidx + q0 + q) : 0;
+          av[g] = q < cnt ? A[(int64_t)kr[g] * ldm + j] : T(0);
+          acc[g] = T(0);
+        }
+        for (int q = 0; q < cnt; ++q) {
+          const int gq = q >> 5, src = q & 31;
+          T mine = T(0);
+          int kq = 0;
+#pragma unroll
+          for (int g = 0; g < kHeadG; ++g)
+            if (g == gq) {
+              mine = av[g] - acc[g];
+              kq = kr[g];
+            }
+          const T uq = shfl(mine, src);
+          kq = shfl(kq, src);
+#pragma unroll
+          for (int g = 0; g < kHeadG; ++g) {
+            if (g == gq && lane == src) av[g] = uq;
+            const int qq = lane + 32 * g;
+            if (qq > q && qq < cnt) acc[g] += A11[kr[g] * h + kq] * uq;
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < kHeadG; ++g)
+          if (lane + 32 * g < cnt) A[(int64_t)kr[g] * ldm + j] = av[g];
+      }
+      __syncthreads();
+      // stage U12 (values, columns, per-panel offsets) for phase C
+      for (int kr = warp; kr < h; kr += nwarps) {
+        const int q0 = __ldg(d.uoff + kr * np1), o = __ldg(d.u12off + kr);
+        const int cnt = __ldg(d.uptr + kr + 1) - q0;
+        const T* Ak = A + (int64_t)kr * ldm;
+        for (int q = lane; q < cnt; q += 32) {
+          const int j = __ldg(d.uidx + q0 + q);
+          su_val[o + q] = Ak[j];
+          su_col[o + q] = (unsigned short)(j - h);
+        }
+        for (int b = lane; b < np1; b += 32) su_off[kr * np1 + b] = o + __ldg(d.uoff + kr * np1 + b) - q0;
+      }
+      __syncthreads();
+    } else {
+      // pivot by pivot, Schur complement applied immediately
+      for (int kp = 0; kp < h; ++kp) {
+        const T inv = T(1) / A[(int64_t)kp * ldm + kp];
+        const int l0 = __ldg(d.lptr + kp), l1 = __ldg(d.lptr + kp + 1);
+        for (int p = l0 + tid; p < l1; p += nthr) A[(int64_t)__ldg(d.lidx + p) * ldm + kp] *= inv;
+        __syncthreads();
+        if (tid == 0) A[(int64_t)kp * ldm + kp] = inv;
+        const int u0 = __ldg(d.uptr + kp), nU = __ldg(d.uptr + kp + 1) - u0;
+        const T* Ak = A + (int64_t)kp * ldm;
+        for (int a = l0 + warp; a < l1; a += nwarps) {
+          T* Ai = A + (int64_t)__ldg(d.lidx + a) * ldm;
+          const T l = Ai[kp];
+          for (int b = lane; b < nU; b += 32) {
+            const int j = __ldg(d.uidx + u0 + b);
+            Ai[j] -= l * Ak[j];
+          }
+        }
+        __syncthreads();
+      }
     }
-    // dense trailing block: blocked right-looking LU
-    for (int p0 = h; p0 < n; p0 += kNB) {
+    // ---- phase C: dense trailing block, blocked right-looking LU
+    for (int pb = 0; pb * kNB < nt; ++pb) {
+      const int p0 = h + pb * kNB;
       const int w = min(kNB, n - p0), m = n - p0, r = m - w;
-      for (int i = tid; i < m * w; i += nthr) {
-        const int a = i / w, b = i - a * w;
-        P[a * PP + b] = A[(int64_t)(p0 + a) * ldm + p0 + b];
+#pragma unroll 4
+      for (int a = warp; a < m; a += nwarps)
+        if (lane < w) Pt[lane * pitch + a] = A[(int64_t)(p0 + a) * ldm + p0 + lane];
+      for (int a = m + tid; a < pitch; a += nthr)
+        for (int b = 0; b < w; ++b) Pt[b * pitch + a] = T(0);
+      __syncthreads();
+      if (plan.head_smem && h > 0) {
+        // pending head contributions -sum_k l_ik u_kj to the panel; each
+        // thread owns rows, its (k, l) pairs come in batches of 8 independent
+        // loads from the compact L21 copy
+        for (int a = tid; a < m; a += nthr) {
+          const int i = p0 + a;
+          const int o = __ldg(d.lrhoff + i - h), cnt = __ldg(d.lrhead + i - h);
+          for (int q0 = 0; q0 < cnt; q0 += 8) {
+            int kb[8];
+            T lb[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const bool ok = q0 + u < cnt;
+              kb[u] = ok ? (__ldg(d.lrhk + o + q0 + u)) : 0;
+              lb[u] = ok ? l21[o + q0 + u] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (q0 + u >= cnt) break;
+              const int e1 = su_off[kb[u] * np1 + pb + 1];
+              for (int e = su_off[kb[u] * np1 + pb]; e < e1; ++e)
+                Pt[((int)su_col[e] + h - p0) * pitch + a] -= lb[u] * su_val[e];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      for (int kk = 0; kk < w; ++kk) {
+        // row kk is final after the previous barrier; the inverse pivot is
+        // stored after this step's barrier (no later step reads it)
+        const T inv = T(1) / Pt[kk * pitch + kk];
+        for (int a = kk + 1 + tid; a < m; a += nthr) {
+          const T l = Pt[kk * pitch + a] * inv;
+          Pt[kk * pitch + a] = l;
+          for (int b = kk + 1; b < w; ++b) Pt[b * pitch + a] -= l * Pt[b * pitch + kk];
+        }
+        __syncthreads();
+        if (tid == 0) Pt[kk * pitch + kk] = inv;
       }
       __syncthreads();
-      for (int kk = 0; kk < w; ++kk) {
-        const T inv = T(1) / P[kk * PP + kk];
-        for (int i = kk + 1 + tid; i < m; i += nthr) P[i * PP + kk] *= inv;
-        __syncthreads();
-        const int cols = w - kk - 1;
-        if (cols > 0)
-          for (int i = tid; i < (m - kk - 1) * cols; i += nthr) {
-            const int a = kk + 1 + i / cols, b = kk + 1 + i % cols;
-            P[a * PP + b] -= P[a * PP + kk] * P[kk * PP + b];
-          }
-        if (tid == 0) P[kk * PP + kk] = inv;
-        __syncthreads();
-      }
-      for (int i = tid; i < m * w; i += nthr) {
-        const int a = i / w, b = i - a * w;
-        A[(int64_t)(p0 + a) * ldm + p0 + b] = P[a * PP + b];
-      }
+      for (int a = warp; a < m; a += nwarps)
+        if (lane < w) A[(int64_t)(p0 + a) * ldm + p0 + lane] = Pt[lane * pitch + a];
       if (r > 0) {
-        // U12 = L11^-1 A12, one thread per column
-        for (int i = tid; i < w * r; i += nthr) {
-          const int a = i / r, b = i - a * r;
-          U[a * r + b] = A[(int64_t)(p0 + a) * ldm + p0 + w + b];
-        }
+        const int rp = round_up(r, 4);
+        for (int a = warp; a < w; a += nwarps)
+          for (int b = lane; b < rp; b += 32)
+            U[a * upitch + b] = b < r ? A[(int64_t)(p0 + a) * ldm + p0 + w + b] : T(0);
         __syncthreads();
-        for (int b = tid; b < r; b += nthr) {
-          for (int kk = 0; kk < w; ++kk) {
-            const T u = U[kk * r + b];
-            for (int a = kk + 1; a < w; ++a) U[a * r + b] -= P[a * PP + kk] * u;
+        if (plan.head_smem && h > 0) {
+          // pending head contributions to the rows of the U block (warp per row)
+          for (int a = warp; a < w; a += nwarps) {
+            const int i = p0 + a;
+            const int o = __ldg(d.lrhoff + i - h), cnt = __ldg(d.lrhead + i - h);
+            for (int q = 0; q < cnt; ++q) {
+              const int kc = __ldg(d.lrhk + o + q);
+              const T l = l21[o + q];
+              const int e1 = su_off[kc * np1 + plan.n_panels];
+              for (int e = su_off[kc * np1 + pb + 1] + lane; e < e1; e += 32)
+                U[a * upitch + ((int)su_col[e] + h - p0 - w)] -= l * su_val[e];
+              __syncwarp();
+            }
           }
-          for (int a = 0; a < w; ++a) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * r + b];
+          __syncthreads();
+        }
+        // U12 = L11^-1 A12, one thread per column
+        if (w == kNB) {
+          for (int b = tid; b < r; b += nthr) {
+            T col[kNB];
+#pragma unroll
+            for (int a = 0; a < kNB; ++a) col[a] = U[a * upitch + b];
+#pragma unroll
+            for (int kk = 0; kk < kNB; ++kk)
+#pragma unroll
+              for (int a = kk + 1; a < kNB; ++a) col[a] -= Pt[kk * pitch + a] * col[kk];
+#pragma unroll
+            for (int a = 0; a < kNB; ++a) U[a * upitch + b] = col[a];
+          }
+        } else {
+          for (int b = tid; b < r; b += nthr)
+            for (int kk = 0; kk < w; ++kk) {
+              const T u = U[kk * upitch + b];
+              for (int a = kk + 1; a < w; ++a) U[a * upitch + b] -= Pt[kk * pitch + a] * u;
+            }
         }
         __syncthreads();
-        // A22 -= L21 U12, tiles of (16 kTM) x (16 kTN)
+        for (int a = warp; a < w; a += nwarps)
+          for (int b = lane; b < r; b += 32) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * upitch + b];
+        // A22 -= L21 U12; L21 column kk is Pt[kk * pitch + w + i]
         const int ty = tid / 16, tx = tid % 16;
-        constexpr int BM = 16 * kTM, BN = 16 * kTN;
-        for (int t0 = 0; t0 < r; t0 += BM)
-          for (int u0 = 0; u0 < r; u0 += BN) {
-            T acc[kTM][kTN];
+        for (int t0 = 0; t0 < r; t0 += kBM)
+          for (int u0 = 0; u0 < r; u0 += kBN) {
             const int i0 = t0 + ty * kTM, j0 = u0 + tx * kTN;
+            if (i0 >= r || j0 >= r) continue;
+            T acc[kTM][kTN];
 #pragma unroll
             for (int a = 0; a < kTM; ++a)
 #pragma unroll
               for (int b = 0; b < kTN; ++b)
                 acc[a][b] = (i0 + a < r && j0 + b < r)
                                 ? A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] : T(0);
+            const T* lp = Pt + w + i0;
+            const T* up = U + j0;
             for (int kk = 0; kk < w; ++kk) {
-              T lv[kTM], uv[kTN];
-#pragma unroll
-              for (int a = 0; a < kTM; ++a) lv[a] = (i0 + a < r) ? P[(w + i0 + a) * PP + kk] : T(0);
-#pragma unroll
-              for (int b = 0; b < kTN; ++b) uv[b] = (j0 + b < r) ? U[kk * r + j0 + b] : T(0);
+              Vec4<T> lv, uv;
+              lv.load(lp + kk * pitch);
+              uv.load(up + kk * upitch);
 #pragma unroll
               for (int a = 0; a < kTM; ++a)
 #pragma unroll
-                for (int b = 0; b < kTN; ++b) acc[a][b] -= lv[a] * uv[b];
+                for (int b = 0; b < kTN; ++b) acc[a][b] -= lv.a[a] * uv.a[b];
             }
 #pragma unroll
             for (int a = 0; a < kTM; ++a)
@@ -385,6 +647,172 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(Dev d, const d
 // ---------------------------------------------------------------------------
 constexpr int kSolveWarps = 4;
 
+// sum_{c in [c0, c1)} row[c] * x[c]: scalar ends, 16-byte vector middle.
+__device__ __forceinline__ float dense_dot(const float* __restrict__ row, const float* x, int c0, int c1) {
+  float s0 = 0.f, s1 = 0.f;
+  int c = c0;
+  for (; c < c1 && (c & 3); ++c) s0 += row[c] * x[c];
+  for (; c + 4 <= c1; c += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(row + c);
+    const float4 b = *reinterpret_cast<const float4*>(x + c);
+    s0 = fmaf(a.x, b.x, s0);
+    s1 = fmaf(a.y, b.y, s1);
+    s0 = fmaf(a.z, b.z, s0);
+    s1 = fmaf(a.w, b.w, s1);
+  }
+  for (; c < c1; ++c) s0 += row[c] * x[c];
+  return s0 + s1;
+}
+__device__ __forceinline__ double dense_dot(const double* __restrict__ row, const double* x, int c0, int c1) {
+  double s0 = 0.0, s1 = 0.0;
+  int c = c0;
+  for (; c < c1 && (c & 1); ++c) s0 += row[c] * x[c];
+  for (; c + 2 <= c1; c += 2) {
+    const double2 a = *reinterpret_cast<const double2*>(row + c);
+    const double2 b = *reinterpret_cast<const double2*>(x + c);
+    s0 = fma(a.x, b.x, s0);
+    s1 = fma(a.y, b.y, s1);
+  }
+  for (; c < c1; ++c) s0 += row[c] * x[c];
+  return s0 + s1;
+}
+
+// Substitution with the factors of one cell (warp per cell).  Sparse head rows
+// run one row at a time with the next row's entries already in flight; the
+// dense tail runs in blocks of 32 rows, one row per lane: each lane streams
+// its row segment left (forward) or right (backward) of the block, then the
+// 32 x 32 diagonal block is resolved with warp shuffles.
+template <class T>
+__device__ void lu_substitute(const Dev& d, const T* __restrict__ A, T* x, int lane) {
+  const int n = d.n, ldm = d.ldm, h = d.head;
+  constexpr int EPL = 4;   // head-row entries per lane (rows up to 128 entries)
+  // forward, sparse head rows (unit lower triangle)
+  {
+    T v[EPL];
+    int j[EPL];
+    auto load_row = [&](int i) {
+      const int p0 = __ldg(d.lrptr + i), p1 = __ldg(d.lrptr + i + 1);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = p0 + lane + 32 * e;
+        j[e] = p < p1 ? __ldg(d.lridx + p) : -1;
+        v[e] = p < p1 ? A[(int64_t)i * ldm + j[e]] : T(0);
+      }
+    };
+    if (h > 0) load_row(0);
+    for (int i = 0; i < h; ++i) {
+      T vc[EPL];
+      int jc[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) { vc[e] = v[e]; jc[e] = j[e]; }
+      if (i + 1 < h) load_row(i + 1);
+      T s = T(0);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e)
+        if (jc[e] >= 0) s += vc[e] * x[jc[e]];
+      // rows longer than EPL * 32 entries finish here
+      for (int p = __ldg(d.lrptr + i) + lane + 32 * EPL; p < __ldg(d.lrptr + i + 1); p += 32) {
+        const int cc = __ldg(d.lridx + p);
+        s += A[(int64_t)i * ldm + cc] * x[cc];
+      }
+      s = warp_sum(s);
+      if (lane == 0) x[i] -= s;
+      __syncwarp();
+    }
+  }
+  // forward, dense tail in blocks of 32 rows
+  for (int r0 = h; r0 < n; r0 += 32) {
+    const int i = r0 + lane;
+    const bool live = i < n;
+    T xi = T(0);
+    T lrow[32];
+    if (live) {
+      const T* Ai = A + (int64_t)i * ldm;
+      T s = T(0);
+      for (int p = __ldg(d.lrptr + i), p1 = __ldg(d.lrptr + i + 1); p < p1; ++p) {
+        const int c = __ldg(d.lridx + p);
+        if (c >= h) break;
+        s += Ai[c] * x[c];
+      }
+      s += dense_dot(Ai, x, h, r0);
+      xi = x[i] - s;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lrow[k] = (k < lane && r0 + k < n) ? Ai[r0 + k] : T(0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) lrow[k] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const T xk = __shfl_sync(0xffffffffu, xi, k);
+      if (lane > k) xi -= lrow[k] * xk;
+    }
+    if (live) x[i] = xi;
+    __syncwarp();
+  }
+  // backward, dense tail from the last block up
+  const int nb = (n - h + 31) / 32;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int r0 = h + 32 * b, r1 = min(r0 + 32, n);
+    const int i = r0 + lane;
+    const bool live = i < n;
+    T xi = T(0);
+    T urow[32];
+    if (live) {
+      const T* Ai = A + (int64_t)i * ldm;
+      xi = x[i] - dense_dot(Ai, x, r1, n);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) urow[k] = (k >= lane && r0 + k < r1) ? Ai[r0 + k] : T(0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) urow[k] = T(0);
+    }
+#pragma unroll
+    for (int k = 31; k >= 0; --k) {
+      if (lane == k) xi *= urow[k];  // inverse pivot on the diagonal
+      const T xk = __shfl_sync(0xffffffffu, xi, k);
+      if (lane < k) xi -= urow[k] * xk;
+    }
+    if (live) x[i] = xi;
+    __syncwarp();
+  }
+  // backward, sparse head rows
+  {
+    T v[EPL];
+    int j[EPL];
+    auto load_row = [&](int i) {
+      const int p0 = __ldg(d.uptr + i), p1 = __ldg(d.uptr + i + 1);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = p0 + lane + 32 * e;
+        j[e] = p < p1 ? __ldg(d.uidx + p) : -1;
+        v[e] = p < p1 ? A[(int64_t)i * ldm + j[e]] : T(0);
+      }
+    };
+    if (h > 0) load_row(h - 1);
+    for (int i = h - 1; i >= 0; --i) {
+      T vc[EPL];
+      int jc[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) { vc[e] = v[e]; jc[e] = j[e]; }
+      const T piv = A[(int64_t)i * ldm + i];
+      if (i > 0) load_row(i - 1);
+      T s = T(0);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e)
+        if (jc[e] >= 0) s += vc[e] * x[jc[e]];
+      // rows longer than EPL * 32 entries finish here
+      for (int p = __ldg(d.uptr + i) + lane + 32 * EPL; p < __ldg(d.uptr + i + 1); p += 32) {
+        const int c = __ldg(d.uidx + p);
+        s += A[(int64_t)i * ldm + c] * x[c];
+      }
+      s = warp_sum(s);
+      if (lane == 0) x[i] = (x[i] - s) * piv;
+      __syncwarp();
+    }
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d) {
   extern __shared__ unsigned char smem_raw[];
@@ -392,8 +820,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * kSolveWarps + wi;
   if (c >= d.C) return;
   if (!(d.flags[c] & F_NEWTON)) return;
-  const int n = d.n, ldm = d.ldm;
-  T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)wi * n;
+  const int n = d.n, xs = (n + 3) / 4 * 4;
+  T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)wi * xs;
   const T* A = static_cast<const T*>(d.lu) + c * d.lu_stride;
   const double a0 = d.alpha[c], h = d.h[c];
   const double inv_a0 = 1.0 / a0;
@@ -404,33 +832,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d) {
     x[__ldg(d.iperm + s)] = T(b);
   }
   __syncwarp();
-  // forward: unit lower triangle, row-oriented
-  for (int i = 0; i < n; ++i) {
-    const int p0 = __ldg(d.lrptr + i), p1 = __ldg(d.lrptr + i + 1);
-    if (p1 == p0) continue;
-    T s = T(0);
-    const T* Ai = A + (int64_t)i * ldm;
-    for (int p = p0 + lane; p < p1; p += 32) {
-      const int kk = __ldg(d.lridx + p);
-      s += Ai[kk] * x[kk];
-    }
-    s = warp_sum(s);
-    if (lane == 0) x[i] -= s;
-    __syncwarp();
-  }
-  // backward: upper triangle with inverse pivots on the diagonal
-  for (int kp = n - 1; kp >= 0; --kp) {
-    const int u0 = __ldg(d.uptr + kp), u1 = __ldg(d.uptr + kp + 1);
-    const T* Ak = A + (int64_t)kp * ldm;
-    T s = T(0);
-    for (int p = u0 + lane; p < u1; p += 32) {
-      const int j = __ldg(d.uidx + p);
-      s += Ak[j] * x[j];
-    }
-    s = warp_sum(s);
-    if (lane == 0) x[kp] = (x[kp] - s) * Ak[kp];
-    __syncwarp();
-  }
+  lu_substitute<T>(d, A, x, lane);
   const double gamma = d.gam[c], gJ = d.gam_J[c];
   const double scale = gamma != gJ ? 2.0 / (1.0 + gamma / gJ) : 1.0;
   double acc = 0.0;
@@ -642,7 +1044,7 @@ struct sm_state {
   int64_t cap = 0, C = 0, ld = 0;
   double t_end = 0.0;
   Dev d{};
-  DevArray scal_d, scal_i, vec, lu, list, counters, scratch;
+  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, l21;
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int* h_counters = nullptr;  // pinned
@@ -650,6 +1052,7 @@ struct sm_state {
   const double* graph_k = nullptr;
   int64_t graph_ldk = 0, graph_C = 0;
   int refresh_ctas = 0;
+  RefreshPlan plan{};
   // instrumentation
   int64_t launches = 0, timed = 0;
   double timed_ms = 0.0;
@@ -710,6 +1113,7 @@ void free_state(sm_state* st) {
   st->list.release();
   st->counters.release();
   st->scratch.release();
+  st->l21.release();
   if (st->h_counters) cudaFreeHost(st->h_counters);
   if (st->ev_in) cudaEventDestroy(st->ev_in);
   if (st->ev_out) cudaEventDestroy(st->ev_out);
@@ -767,10 +1171,9 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   predict_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_PREDICT, false, s)) != SM_OK) return r;
   if ((r = time_mark(st, SM_TIME_REFRESH, true, s)) != SM_OK) return r;
-  refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, refresh_smem_bytes(d.n, d.head, sizeof(T)), s>>>(
-      d, k, ldk);
+  refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(d, k, ldk, st->plan);
   if ((r = time_mark(st, SM_TIME_REFRESH, false, s)) != SM_OK) return r;
-  const size_t smem = sizeof(T) * (size_t)kSolveWarps * d.n;
+  const size_t smem = sizeof(T) * (size_t)kSolveWarps * ((d.n + 3) / 4 * 4);
   for (int m = 0; m < d.newton_max; ++m) {
     if ((r = time_mark(st, SM_TIME_RHS, true, s)) != SM_OK) return r;
     r = launch_rhs_masked(net, d.C, k, ldk, d.y, d.f, d.ld, st->scratch.as<double>(), d.ld, d.flags,
@@ -960,6 +1363,12 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.lptr = lu.d_lptr.as<int>(); d.lidx = lu.d_lidx.as<int>();
   d.uptr = lu.d_uptr.as<int>(); d.uidx = lu.d_uidx.as<int>();
   d.lrptr = lu.d_lrptr.as<int>(); d.lridx = lu.d_lridx.as<int>();
+  d.ucptr = lu.d_ucptr.as<int>(); d.ucidx = lu.d_ucidx.as<int>();
+  d.jrc = lu.d_jrc.as<int>(); d.uoff = lu.d_uoff.as<int>(); d.lrhead = lu.d_lrhead.as<int>();
+  d.lrhoff = lu.d_lrhoff.as<int>();
+  d.u12off = lu.d_u12off.as<int>();
+  d.lrhk = lu.d_lrhk.as<int>();
+  d.jt_slot = net->d_jt_slot.as<int2>(); d.reac = net->d_reac.as<int2>();
   d.jp_ptr = net->d_jp_ptr.as<int>(); d.jt_ptr = net->d_jt_ptr.as<int>();
   d.jt_word = net->d_jt_word.as<int2>(); d.jpos = lu.d_jpos.as<int>();
   if (cudaStreamCreateWithFlags(&st->s, cudaStreamNonBlocking) != cudaSuccess) return fail(SM_ECUDA);
@@ -968,9 +1377,38 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   if (cudaMallocHost(&st->h_counters, 4 * sizeof(int)) != cudaSuccess) return fail(SM_ENOMEM);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device);
-  const size_t rsm = refresh_smem_bytes(n, lu.head, esz);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device);
+  {
+    // shared memory of the refresh kernel: the largest of its three phases
+    RefreshPlan& pl = st->plan;
+    const int nt = n - lu.head;
+    pl.pitch = round_up(nt + 4, 4);  // rows past the panel height: zero padding for 4-wide loads
+    pl.n_panels = (nt + kNB - 1) / kNB;
+    pl.upitch = round_up(std::max(nt - kNB, 4), 4);
+    pl.n_l21 = lu.lrhoff.empty() ? 0 : lu.lrhoff.back();
+    pl.n_u12 = 0;
+    for (int k2 = 0; k2 < lu.head; ++k2) pl.n_u12 += lu.uptr[k2 + 1] - lu.uoff[(size_t)k2 * (pl.n_panels + 1)];
+    const size_t stage_u12 = (esz + 2) * (size_t)pl.n_u12 + sizeof(int) * (size_t)lu.head * (pl.n_panels + 1) + 16;
+    const size_t tail = esz * (size_t)kNB * (pl.pitch + pl.upitch) + stage_u12;
+    const size_t stage = sizeof(double) * (2 * (size_t)net->n_r + 256) + sizeof(float) * 2 * (size_t)n;
+    const size_t a11 = esz * (size_t)lu.head * lu.head;
+    int max_l21 = 0, max_u12 = 0;
+    for (int i = lu.head; i < n; ++i) {
+      int cnt = 0;
+      for (int p = lu.lrptr[i]; p < lu.lrptr[i + 1] && lu.lridx[p] < lu.head; ++p) ++cnt;
+      max_l21 = std::max(max_l21, cnt);
+    }
+    for (int j = 0; j + 1 < (int)lu.ucptr.size(); ++j) max_u12 = std::max(max_u12, lu.ucptr[j + 1] - lu.ucptr[j]);
+    // A11 must not overlap the staged U12 (written while A11 is still read)
+    const size_t head_b = esz * (size_t)kNB * (pl.pitch + pl.upitch) + stage_u12;
+    pl.head_smem = lu.head > 0 && a11 <= esz * (size_t)kNB * (pl.pitch + pl.upitch) &&
+                   head_b <= (size_t)smem_max && max_l21 <= kHeadLanes && max_u12 <= kHeadLanes;
+    pl.bytes = std::max(tail, stage);
+    if (pl.head_smem) pl.bytes = std::max(pl.bytes, a11);
+  }
+  const size_t rsm = st->plan.bytes;
+
   if ((int64_t)rsm > smem_max) return fail(SM_ENOTSUP);
   if (d.mixed) {
     SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
@@ -984,6 +1422,10 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<double>, kRefreshThreads, rsm);
   }
   st->refresh_ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  // compact L21 copies, one per refresh CTA (the grid is exactly refresh_ctas)
+  if ((r = st->l21.ensure(esz * (size_t)std::max(st->plan.n_l21, 1) * (size_t)st->refresh_ctas)) != SM_OK)
+    return fail(r);
+  d.l21_scratch = st->l21.p;
   SM_TRY_CUDA(cudaMemset(st->scal_i.p, 0, st->scal_i.bytes));
   *out = st;
   return SM_OK;
@@ -1000,7 +1442,7 @@ sm_status sm_state_free(sm_state* st) {
 sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
   if (!st || !bytes) return SM_EINVAL;
   *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->list.bytes +
-           st->counters.bytes + st->scratch.bytes;
+           st->counters.bytes + st->scratch.bytes + st->l21.bytes;
   return SM_OK;
 }
 

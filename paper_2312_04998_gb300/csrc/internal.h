@@ -67,9 +67,18 @@ struct LUSymbolic {
   std::vector<int32_t> lptr, lidx;        // per pivot: rows below it (positions)
   std::vector<int32_t> uptr, uidx;        // per pivot: columns right of it
   std::vector<int32_t> lrptr, lridx;      // per row: columns of L left of the diagonal
+  std::vector<int32_t> ucptr, ucidx;      // per tail column j >= head: head rows k with U(k, j) != 0
+  std::vector<int32_t> jrc;               // per J pattern entry: (row position << 16) | column position
+  std::vector<int32_t> lrhead;            // per tail row: entries of its L row in head columns
+  std::vector<int32_t> lrhoff;            // exclusive prefix sum of lrhead (n - head + 1 entries)
+  std::vector<int32_t> u12off;            // per head row: start of its tail-column U entries, packed
+  std::vector<int32_t> lrhk;              // head column of each L21 entry in compact row order
+  std::vector<int32_t> uoff;              // per head row k: [n_panels + 1] offsets into its U list where
+                                          // the tail columns of each 32-wide panel start
   std::vector<int32_t> jpos;              // per J pattern entry: dense offset p*ld+q
   int64_t nnz = 0, flops = 0;
-  DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_jpos, d_perm, d_iperm;
+  DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_ucptr, d_ucidx, d_jpos, d_perm, d_iperm,
+      d_jrc, d_uoff, d_lrhead, d_lrhoff, d_u12off, d_lrhk;
 };
 
 struct sm_net {
@@ -95,6 +104,7 @@ struct sm_net {
   DevArray d_reac;        // int2 per reaction: reactant indices (-1 = none)
   DevArray d_rate;        // RatePar per reaction: (log alpha | alpha, beta, gamma, class)
   DevArray d_jp_ptr, d_jt_ptr, d_jt_word;  // Jacobian gather lists
+  DevArray d_jt_slot;                      // (reaction | coef << 24, reactant slot) per term
   std::vector<int32_t> jchunk;             // J entries per gather chunk (balanced by terms)
   DevArray d_jchunk;
   DevArray d_status;      // int32 device status word

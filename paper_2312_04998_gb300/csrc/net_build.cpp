@@ -276,10 +276,57 @@ void build_lu_symbolic(sm_net& net) {
       break;
     }
   }
+  // column-wise view of the U entries of head rows in tail columns
+  {
+    const int32_t h = lu.head;
+    std::vector<std::vector<int32_t>> cols(n);
+    for (int32_t k = 0; k < h; ++k)
+      for (int32_t p = lu.uptr[k]; p < lu.uptr[k + 1]; ++p)
+        if (lu.uidx[p] >= h) cols[lu.uidx[p]].push_back(k);
+    lu.ucptr.assign(1, 0);
+    lu.ucidx.clear();
+    for (int32_t j = h; j < n; ++j) {
+      lu.ucidx.insert(lu.ucidx.end(), cols[j].begin(), cols[j].end());
+      lu.ucptr.push_back((int32_t)lu.ucidx.size());
+    }
+  }
+  // per head row: where each 32-wide tail panel's columns start in its U list
+  {
+    const int32_t h = lu.head, np = (n - h + 31) / 32;
+    lu.uoff.assign((size_t)h * (np + 1), 0);
+    for (int32_t k = 0; k < h; ++k)
+      for (int32_t b = 0; b <= np; ++b) {
+        const int32_t c0 = h + 32 * b;
+        int32_t p = lu.uptr[k];
+        while (p < lu.uptr[k + 1] && lu.uidx[p] < c0) ++p;
+        lu.uoff[(size_t)k * (np + 1) + b] = p;
+      }
+  }
+  lu.lrhead.assign(n - lu.head, 0);
+  for (int32_t i = lu.head; i < n; ++i) {
+    int32_t cnt = 0;
+    for (int32_t p = lu.lrptr[i]; p < lu.lrptr[i + 1] && lu.lridx[p] < lu.head; ++p) ++cnt;
+    lu.lrhead[i - lu.head] = cnt;
+  }
+  lu.lrhoff.assign(1, 0);
+  for (int32_t v : lu.lrhead) lu.lrhoff.push_back(lu.lrhoff.back() + v);
+  lu.lrhk.clear();
+  for (int32_t i = lu.head; i < n; ++i)
+    for (int32_t q = 0; q < lu.lrhead[i - lu.head]; ++q) lu.lrhk.push_back(lu.lridx[lu.lrptr[i] + q]);
+  {
+    const int32_t np1 = (n - lu.head + 31) / 32 + 1;
+    lu.u12off.assign(1, 0);
+    for (int32_t k = 0; k < lu.head; ++k)
+      lu.u12off.push_back(lu.u12off.back() + lu.uptr[k + 1] - lu.uoff[(size_t)k * np1]);
+  }
   lu.jpos.resize(net.jp_col.size());
+  lu.jrc.resize(net.jp_col.size());
   for (int32_t i = 0; i < n; ++i)
     for (int32_t p = net.jp_ptr[i]; p < net.jp_ptr[i + 1]; ++p)
+    {
       lu.jpos[p] = lu.iperm[i] * lu.ld + lu.iperm[net.jp_col[p]];
+      lu.jrc[p] = (lu.iperm[i] << 16) | lu.iperm[net.jp_col[p]];
+    }
 }
 
 }  // namespace
@@ -554,6 +601,21 @@ sm_status net_upload(sm_net* net) {
   if ((st = net->d_jp_ptr.upload(net->jp_ptr.data(), net->jp_ptr.size() * 4)) != SM_OK) return st;
   if ((st = net->d_jt_ptr.upload(net->jt_ptr.data(), net->jt_ptr.size() * 4)) != SM_OK) return st;
   if ((st = net->d_jt_word.upload(words.data(), words.size() * 4)) != SM_OK) return st;
+  // the same terms with the reactant slot whose derivative they use: slot 0 =
+  // d/d(first reactant) = k' x_second (or k'), slot 1 = d/d(second reactant)
+  {
+    std::vector<int32_t> ws(2 * net->jt_rx.size());
+    for (int32_t i = 0; i < net->n_s; ++i)
+      for (int32_t e = net->jp_ptr[i]; e < net->jp_ptr[i + 1]; ++e) {
+        const int32_t l = net->jp_col[e];
+        for (int32_t t = net->jt_ptr[e]; t < net->jt_ptr[e + 1]; ++t) {
+          const int32_t j = net->jt_rx[t];
+          ws[2 * t] = (int32_t)pack(j, net->jt_coef[t]);
+          ws[2 * t + 1] = net->reac[2 * j] == l ? 0 : 1;
+        }
+      }
+    if ((st = net->d_jt_slot.upload(ws.data(), ws.size() * 4)) != SM_OK) return st;
+  }
   // gather chunks of about equal term count over the J pattern entries
   {
     const int64_t n_e = (int64_t)net->jp_col.size(), n_t = (int64_t)net->jt_rx.size();
@@ -575,7 +637,16 @@ sm_status net_upload(sm_net* net) {
   if (!lu.uidx.empty() && (st = lu.d_uidx.upload(lu.uidx.data(), lu.uidx.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_lrptr.upload(lu.lrptr.data(), lu.lrptr.size() * 4)) != SM_OK) return st;
   if (!lu.lridx.empty() && (st = lu.d_lridx.upload(lu.lridx.data(), lu.lridx.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_ucptr.upload(lu.ucptr.data(), lu.ucptr.size() * 4)) != SM_OK) return st;
+  if (!lu.ucidx.empty() && (st = lu.d_ucidx.upload(lu.ucidx.data(), lu.ucidx.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_jpos.upload(lu.jpos.data(), lu.jpos.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_jrc.upload(lu.jrc.data(), lu.jrc.size() * 4)) != SM_OK) return st;
+  if (!lu.uoff.empty() && (st = lu.d_uoff.upload(lu.uoff.data(), lu.uoff.size() * 4)) != SM_OK) return st;
+  if (!lu.lrhead.empty() && (st = lu.d_lrhead.upload(lu.lrhead.data(), lu.lrhead.size() * 4)) != SM_OK)
+    return st;
+  if ((st = lu.d_lrhoff.upload(lu.lrhoff.data(), lu.lrhoff.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_u12off.upload(lu.u12off.data(), lu.u12off.size() * 4)) != SM_OK) return st;
+  if (!lu.lrhk.empty() && (st = lu.d_lrhk.upload(lu.lrhk.data(), lu.lrhk.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_perm.upload(lu.perm.data(), lu.perm.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_iperm.upload(lu.iperm.data(), lu.iperm.size() * 4)) != SM_OK) return st;
   int32_t zero = 0;
