@@ -222,7 +222,13 @@ typedef struct {
     int32_t use_graph;        /* capture the attempt loop in a CUDA graph (1) or not */
     int32_t attempts_per_sync;/* attempts launched between completion checks      */
     int32_t timing_kind;      /* SM_TIME_*: kernel class timed with CUDA events    */
+    int32_t record_steps;     /* > 0: record up to this many accepted steps per cell
+                                 (times, sizes, orders) and the step history every
+                                 SM_CHECKPOINT_EVERY steps, for sm_adjoint         */
 } sm_opts;
+
+/* Accepted steps between stored states of the recorded forward run. */
+#define SM_CHECKPOINT_EVERY 16
 
 /* Kernel classes of the integrator whose launches sm_state_timing reports. */
 enum { SM_TIME_NONE = 0, SM_TIME_REFRESH = 1, SM_TIME_RHS = 2, SM_TIME_SOLVE = 3,
@@ -284,6 +290,57 @@ sm_status sm_state_read(sm_state* st, double* d_y, int64_t ld, sm_cell_stats* d_
  * used; sm_state_timing_reset zeroes the totals.  Any pointer may be NULL. */
 sm_status sm_state_timing(const sm_state* st, int64_t* launches, double* ms, int64_t* timed);
 sm_status sm_state_timing_reset(sm_state* st);
+
+/* ---- Sensitivities: discrete adjoint of the BDF integration -----------------
+ * The paper integrates the network but computes no derivatives; these calls
+ * are the library's addition.  They differentiate the frozen-step map of the
+ * last recorded run (opts.record_steps > 0): the accepted steps (t_m, h_m,
+ * q_m), m = 1..N, are held fixed and every implicit BDF equation
+ *   alpha_0^m y_m + sum_{i=1..q_m} alpha_i^m y_{m-i} - h_m f(y_m; k) = 0
+ * (alpha from the step times, as in the integrator) is taken as solved
+ * exactly.  For Phi = c^T y_N, backwards in m,
+ *   (alpha_0^m I - h_m J(y_m))^T lambda_m = c [m = N] - sum_{m'} alpha_{m'-m}^{m'} lambda_{m'}
+ * over the later steps m' with m' - m <= q_{m'}, and
+ *   dPhi / d log k_j = sum_m h_m R_j(y_m) (S^T lambda_m)_j
+ * because f = S R (Eq. 7) and each R_j is proportional to k_j. */
+
+/* Largest number of cotangents per sm_adjoint call. */
+#define SM_ADJ_MAX_COT 64
+
+/* Copies the recorded step log of the state's last run: d_t[m][ld] = t_m (end
+ * time of accepted step m + 1), d_h[m][ld] = h_m, d_q[m][ld] = order, for
+ * m < m_max <= opts.record_steps (device arrays; rows past a cell's step
+ * count are unspecified; the per-cell count is sm_cell_stats.steps).
+ * SM_EINVAL if the state records nothing or m_max is out of range. */
+sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, int32_t* d_q, int64_t ld,
+                         void* stream);
+
+/* Reverse sweep for n_cot cotangents at once (1 <= n_cot <= SM_ADJ_MAX_COT).
+ * d_k     = the k'[n_r][ld] the recorded run was integrated with (device);
+ * d_cot   = c[n_cot][n_s][ld] (device), the weights of y_N for each Phi;
+ * d_grad  = out[n_cot][n_r][ld] (device): dPhi_v / d log k_j per cell;
+ * d_astat = per-cell status (device, C entries, may be NULL): 0 ok, 1 no
+ *           usable record (the cell did not finish with SM_CELL_OK or took
+ *           more than opts.record_steps steps; its gradient is 0), 2 a
+ *           recomputed step's Newton iteration did not reach its tolerance
+ *           (the gradient is computed but less accurate).
+ * Work and memory: segments of SM_CHECKPOINT_EVERY steps are recomputed from
+ * the stored step history (last first), each recomputed state gets its own
+ * FP64 factorisation, then the segment is swept backwards.  The workspace is
+ * library-owned, grown on the first call and kept with the state: about
+ * SM_CHECKPOINT_EVERY * n_s * ldm * 8 bytes per cell of a pass (ldm = n_s
+ * rounded up to a multiple of 8) plus the cotangent vectors; cells_per_pass
+ * (0 = all cells in one pass; otherwise rounded up to a multiple of 32)
+ * bounds it.  The call overwrites the integrator's working vectors (the
+ * history): read the solution first, and call sm_state_init or sm_integrate
+ * before stepping again; recorded steps and sm_cell_stats stay valid.
+ * Errors: SM_EINVAL (bad arguments, or the state records nothing),
+ * SM_ENOTSUP (a state created with SM_PREC_MIXED: the adjoint runs in FP64
+ * only), SM_ENOMEM (workspace does not fit: use a smaller cells_per_pass);
+ * SM_EPARTIAL if any cell's d_astat is not 0.  Synchronises the host with the
+ * state's stream once per pass. */
+sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* d_cot, int32_t n_cot,
+                     double* d_grad, int32_t* d_astat, int64_t cells_per_pass, void* stream);
 
 /* Wait for all work on `stream` and report (and clear) any error a kernel of
  * this network wrote to its device status word. */

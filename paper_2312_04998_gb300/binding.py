@@ -53,7 +53,7 @@ class Opts_c(ct.Structure):
                 ("q_max", ct.c_int32), ("max_steps", ct.c_int32), ("j_age_max", ct.c_int32),
                 ("newton_max", ct.c_int32), ("max_conv_fails", ct.c_int32), ("precision", ct.c_int32),
                 ("use_graph", ct.c_int32), ("attempts_per_sync", ct.c_int32),
-                ("timing_kind", ct.c_int32)]
+                ("timing_kind", ct.c_int32), ("record_steps", ct.c_int32)]
 
 
 CELL_STATS_DTYPE = np.dtype([("status", np.int32), ("steps", np.int32), ("rejects", np.int32),
@@ -98,7 +98,12 @@ _SIGS = [
     ("sm_step_bdf", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p]),
     ("sm_state_read", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p,
                                    ct.POINTER(ct.c_int64), ct.c_void_p]),
+    ("sm_state_steps", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                    ct.c_int64, ct.c_void_p]),
+    ("sm_adjoint", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int32,
+                                ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
 ]
+ADJ_MAX_COT = 64
 
 
 def lib():
@@ -316,6 +321,36 @@ class State:
                                    _dptr(stats) if stats is not None else None, ct.byref(running),
                                    _stream(dev)), "sm_state_read")
         return running.value
+
+
+    def steps_log(self, m_max, C=None):
+        """Recorded accepted steps: device tensors t, h (float64) and q (int32),
+        each [m_max][ld]; row m is step m + 1 of every cell."""
+        import torch
+        C = self.cells if C is None else C
+        ld = pad_ld(C)
+        dev = torch.device("cuda", self.net.device)
+        t = torch.zeros((m_max, ld), dtype=torch.float64, device=dev)
+        h = torch.zeros((m_max, ld), dtype=torch.float64, device=dev)
+        q = torch.zeros((m_max, ld), dtype=torch.int32, device=dev)
+        _check(lib().sm_state_steps(self.h, int(m_max), _dptr(t), _dptr(h), _dptr(q), int(ld), _stream(dev)),
+               "sm_state_steps")
+        return t, h, q
+
+    def adjoint(self, k, cot, grad, astat=None, cells_per_pass=0, allow_partial=True):
+        """Reverse sweep of the last recorded run: cot [n_cot][n_s][ld] ->
+        grad [n_cot][n_r][ld] = dPhi/dlog k per cell (device float64 tensors,
+        same ld as k).  astat: optional device int32 tensor of C entries.
+        Returns SM_OK or SM_EPARTIAL."""
+        ld = int(k.stride(0))
+        assert cot.dim() == 3 and cot.stride(1) == ld and grad.stride(1) == ld
+        code = lib().sm_adjoint(self.h, _dptr(k), ld, _dptr(cot), int(cot.shape[0]), _dptr(grad),
+                                _dptr(astat) if astat is not None else None, int(cells_per_pass),
+                                _stream(k.device))
+        if code == SM_EPARTIAL and allow_partial:
+            return code
+        _check(code, "sm_adjoint")
+        return code
 
 
 def stats_tensor(C, device):

@@ -82,6 +82,8 @@ void release_all(sm_net* net) {
   lu.d_u12off.release();
   lu.d_lrhk.release();
   net->d_jt_slot.release();
+  net->d_sc_ptr.release();
+  net->d_sc_ent.release();
   lu.d_lptr.release();
   lu.d_lidx.release();
   lu.d_uptr.release();

@@ -25,6 +25,7 @@
 namespace {
 
 constexpr int QMAX = 5;  // highest BDF order; the history keeps QMAX + 1 points
+constexpr int kCkpt = SM_CHECKPOINT_EVERY;
 enum : int {
   F_NEED_J = 1, F_REJECTED = 2, F_HAS_EPREV = 4, F_NEWTON = 8, F_CONV = 16,
   F_FINAL = 32, F_REFRESH = 64, F_FAILED = 128, F_ATTEMPT = 256
@@ -42,6 +43,13 @@ struct Dev {
   // per-cell vectors [n][ld]; Y is [QMAX+1][n][ld]
   double *Y, *ypred, *y, *psi, *f, *f0, *eprev, *w, *wf;
   int *list, *counters;  // counters[0] = refresh list length, [1] = running cells
+  // recording (record > 0): per accepted step m (1-based) at [m-1][ld]; the
+  // step history after every kCkpt-th accepted step at checkpoint m / kCkpt
+  int record;
+  double *log_t, *log_h;
+  int* log_q;
+  double *ck_Y, *ck_t;   // [K][QMAX+1][n][ld], [K][QMAX+1][ld]
+  int* ck_nh;            // [K][ld]
   void* lu;
   int64_t lu_stride;
   int ldm;
@@ -49,6 +57,8 @@ struct Dev {
       *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk;
   void* l21_scratch;
   const int2 *jt_word, *jt_slot, *reac;
+  const int* sc_ptr;
+  const uint32_t* sc_ent;
 };
 
 __device__ __forceinline__ double& V(double* a, const Dev& d, int s, int64_t c) {
@@ -120,6 +130,18 @@ __global__ void init_copy_kernel(Dev d, const double* __restrict__ yin, int64_t 
   d.h[c] = 0.0;
 }
 
+// Copies the step history of cell c into checkpoint slot kk.
+__device__ void store_checkpoint(const Dev& d, int64_t c, int kk) {
+  const int nh = d.nh[c];
+  const int64_t vs = (int64_t)d.n * d.ld;
+  double* dst = d.ck_Y + (int64_t)kk * (QMAX + 1) * vs;
+  for (int i = 0; i < nh; ++i) {
+    for (int s = 0; s < d.n; ++s) dst[i * vs + (int64_t)s * d.ld + c] = Yh(d, i)[(int64_t)s * d.ld + c];
+    d.ck_t[((int64_t)kk * (QMAX + 1) + i) * d.ld + c] = d.tn[(int64_t)i * d.ld + c];
+  }
+  d.ck_nh[(int64_t)kk * d.ld + c] = nh;
+}
+
 __global__ void init_finish_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.C) return;
@@ -146,6 +168,7 @@ __global__ void init_finish_kernel(Dev d) {
   d.gam_J[c] = 1.0;
   d.crate[c] = 1.0;
   d.crej[c] = d.ccf[c] = 0;
+  if (d.record) store_checkpoint(d, c, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -814,12 +837,12 @@ __device__ void lu_substitute(const Dev& d, const T* __restrict__ A, T* x, int l
 }
 
 template <class T>
-__global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d) {
+__global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, int need, int want) {
   extern __shared__ unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int64_t c = (int64_t)blockIdx.x * kSolveWarps + wi;
   if (c >= d.C) return;
-  if (!(d.flags[c] & F_NEWTON)) return;
+  if ((d.flags[c] & need) != want) return;   // cells in Newton (and, in replays, on this factor set)
   const int n = d.n, xs = (n + 3) / 4 * 4;
   T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)wi * xs;
   const T* A = static_cast<const T*>(d.lu) + c * d.lu_stride;
@@ -983,6 +1006,15 @@ __global__ void finish_kernel(Dev d) {
   d.nh[c] = nh_new;
   d.t[c] = tnew;
   d.steps[c] += 1;
+  if (d.record) {
+    const int m = d.steps[c];  // 1-based index of this accepted step
+    if (m <= d.record) {
+      d.log_t[(int64_t)(m - 1) * d.ld + c] = tnew;
+      d.log_h[(int64_t)(m - 1) * d.ld + c] = h;
+      d.log_q[(int64_t)(m - 1) * d.ld + c] = q;
+      if (m % kCkpt == 0) store_checkpoint(d, c, m / kCkpt);
+    }
+  }
   d.j_age[c] += 1;
   d.crej[c] = 0;
   d.ccf[c] = 0;
@@ -1033,6 +1065,279 @@ __global__ void count_running_kernel(Dev d) {
   else if (s != SM_CELL_OK) atomicAdd(&d.counters[2], 1);
 }
 
+// ---------------------------------------------------------------------------
+// Discrete adjoint of the frozen-step map (reverse sweep).
+//
+// The recorded accepted steps (t_m, h_m, q_m) of the last integration are
+// fixed and every implicit step alpha_0 y_m + sum_i alpha_i y_{m-i} - h_m f(y_m)
+// = 0 is solved to a tight tolerance.  Segments of kCkpt steps are recomputed
+// from their stored step history, last segment first; each recomputed state
+// y_m gets its own factorisation of M_m = I - gamma_m J(y_m), kept in one of
+// kCkpt slots, which is also the Newton matrix of step m + 1.  Walking the
+// segment backwards, lambda_m solves
+//   (alpha_0^m M_m)^T lambda_m = c [m = N] - sum_d alpha_d^{m+d} lambda_{m+d}
+// over d = 1..QMAX with d <= q_{m+d}, and
+//   dPhi / d log k_j += h_m R_j(y_m) (S^T lambda_m)_j,
+// since f = S R and every R_j is proportional to k_j.
+// Cells are processed in passes of at most `cells_per_pass`; inside a pass
+// the cell index is local (Dev pointers are shifted to the pass's first cell)
+// and the adjoint arrays use their own stride lda.
+// ---------------------------------------------------------------------------
+constexpr int kRing = QMAX + 1;          // lambda history slots, indexed by m mod kRing
+constexpr double kReplayTol = 1e-4;      // Newton tolerance of the recomputed steps (WRMS units)
+constexpr int kReplayIters = 8;
+
+struct AdjDev {
+  int n_cot;
+  double run_tol;               // Newton tolerance of the recorded run
+  int64_t lda;
+  int *N, *K, *seg, *astat;     // [lda]: frozen steps, segments, current segment, status
+  int* seg_q;                   // [kCkpt][lda]
+  int* ring_q;                  // [kRing][lda]
+  double* seg_y;                // [kCkpt][n][lda] recomputed states of the segment
+  double* seg_h;                // [kCkpt][lda]
+  double* seg_alpha;            // [kCkpt][QMAX+1][lda]
+  double* ring_alpha;           // [kRing][QMAX+1][lda]
+  double* lam;                  // [kRing][n_cot][n][lda]
+  double* kc;                   // [Cc][n_r] rate coefficients, cell-major
+  double* g;                    // [Cc][n_cot][n_r] gradient accumulators, cell-major
+  double* slots;                // [kCkpt][Cc][lu_stride] factors of M_m
+  const double* cot;            // [n_cot][n][ldu]
+  int64_t ldu;
+};
+
+__device__ __forceinline__ double* slot_lu(const Dev& d, const AdjDev& a, int j, int64_t c) {
+  return a.slots + ((int64_t)j * d.C + c) * d.lu_stride;
+}
+
+__global__ void adj_setup_kernel(Dev d, AdjDev a, const double* __restrict__ k, int64_t ldk) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int N = d.steps[c];
+  const bool ok = d.status[c] == SM_CELL_OK && N >= 1 && N <= d.record;
+  const int K = ok ? (N + kCkpt - 1) / kCkpt : 0;
+  a.N[c] = ok ? N : 0;
+  a.K[c] = K;
+  a.astat[c] = ok ? 0 : 1;
+  atomicMax(&d.counters[3], K);
+  for (int j = 0; j < d.n_r; ++j) a.kc[c * d.n_r + j] = k[(int64_t)j * ldk + c];
+  for (int64_t i = 0; i < (int64_t)a.n_cot * d.n_r; ++i) a.g[c * a.n_cot * d.n_r + i] = 0.0;
+  for (int i = 0; i < kRing; ++i) a.ring_q[(int64_t)i * a.lda + c] = 0;
+}
+
+// Restores the step history stored before segment K - 1 - rs.
+__global__ void seg_restore_kernel(Dev d, AdjDev a, int rs) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int sg = a.astat[c] == 0 ? a.K[c] - 1 - rs : -1;
+  a.seg[c] = sg;
+  if (sg < 0) return;
+  const int nh = d.ck_nh[(int64_t)sg * d.ld + c];
+  const int64_t vs = (int64_t)d.n * d.ld;
+  const double* src = d.ck_Y + (int64_t)sg * (QMAX + 1) * vs;
+  for (int i = 0; i < nh; ++i) {
+    for (int s = 0; s < d.n; ++s) Yh(d, i)[(int64_t)s * d.ld + c] = src[i * vs + (int64_t)s * d.ld + c];
+    d.tn[(int64_t)i * d.ld + c] = d.ck_t[((int64_t)sg * (QMAX + 1) + i) * d.ld + c];
+  }
+  d.nh[c] = nh;
+}
+
+// Global index m of segment position j for cell c, 0 if the cell has none.
+__device__ __forceinline__ int seg_step(const AdjDev& a, int64_t c, int j) {
+  const int sg = a.seg[c];
+  if (sg < 0) return 0;
+  const int m = sg * kCkpt + 1 + j;
+  return m <= a.N[c] ? m : 0;
+}
+
+// Predictor, BDF coefficients and Newton set-up of frozen step m.
+__global__ void rpredict_kernel(Dev d, AdjDev a, int j) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int m = seg_step(a, c, j);
+  if (!m) {
+    d.flags[c] = 0;
+    return;
+  }
+  const double tnew = d.log_t[(int64_t)(m - 1) * d.ld + c];
+  const double h = d.log_h[(int64_t)(m - 1) * d.ld + c];
+  const int q = d.log_q[(int64_t)(m - 1) * d.ld + c];
+  const int nh = d.nh[c];
+  double T[QMAX + 1], wts[QMAX + 1], al[QMAX + 1];
+  for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
+  const bool lagr = nh > q;
+  if (lagr) lagrange(T, q + 1, tnew, wts);
+  bdf_alphas(tnew, T, q, h, al);
+  d.h[c] = h;
+  d.gam[c] = h / al[0];
+  for (int i = 0; i <= QMAX; ++i) {
+    const double v = i <= q ? al[i] : 0.0;
+    d.alpha[(int64_t)i * d.ld + c] = v;
+    a.seg_alpha[((int64_t)j * (QMAX + 1) + i) * a.lda + c] = v;
+  }
+  a.seg_h[(int64_t)j * a.lda + c] = h;
+  a.seg_q[(int64_t)j * a.lda + c] = q;
+  // the factors at y_{m-1} serve as Newton matrix unless gamma moved too far
+  // from theirs (the integrator's own refresh rule); the segment's first step
+  // always starts from fresh factors at the predictor
+  const bool fresh = j == 0 || fabs(h / al[0] / d.gam_J[c] - 1.0) > d.gamma_tol;
+  d.flags[c] = F_NEWTON | (fresh ? F_REFRESH : 0);
+  d.m_it[c] = 0;
+  d.dprev[c] = 0.0;
+  d.crate[c] = 1.0;
+  for (int s = 0; s < d.n; ++s) {
+    const int64_t o = (int64_t)s * d.ld + c;
+    const double y0 = Yh(d, 0)[o];
+    double yp;
+    if (lagr) {
+      yp = 0.0;
+      for (int i = 0; i <= q; ++i) yp += wts[i] * Yh(d, i)[o];
+    } else {
+      yp = y0 + h * d.f0[o];
+    }
+    double ps = 0.0;
+    for (int i = 1; i <= q; ++i) ps += al[i] * Yh(d, i - 1)[o];
+    d.ypred[o] = yp;
+    d.y[o] = yp;
+    d.psi[o] = ps;
+    d.w[o] = 1.0 / (d.rtol * fabs(y0) + d.atol);
+  }
+}
+
+// Refresh list: the cells that take frozen step j (need_flag = 0), or those
+// of them whose flags contain need_flag.
+__global__ void adj_list_kernel(Dev d, AdjDev a, int j, int need_flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  if (seg_step(a, c, j) && (d.flags[c] & need_flag) == need_flag) d.list[atomicAdd(&d.counters[0], 1)] = (int)c;
+}
+
+// Keeps the solved state for the backward pass and shifts the history; the
+// state also becomes the point at which the next refresh evaluates J.
+__global__ void rcommit_kernel(Dev d, AdjDev a, int j) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int m = seg_step(a, c, j);
+  if (!m) return;
+  // iterations stopped short of the replay tolerance still count when the
+  // last correction met the tolerance the recorded run was solved to
+  if (!(d.flags[c] & F_CONV) && !(d.dprev[c] <= a.run_tol)) a.astat[c] = 2;
+  const int nh = d.nh[c], nh_new = min(nh + 1, d.q_max + 1);
+  for (int s = 0; s < d.n; ++s) {
+    const int64_t o = (int64_t)s * d.ld + c;
+    const double yv = d.y[o];
+    a.seg_y[((int64_t)j * d.n + s) * a.lda + c] = yv;
+    d.ypred[o] = yv;
+    for (int i = nh_new - 1; i >= 1; --i) Yh(d, i)[o] = Yh(d, i - 1)[o];
+    Yh(d, 0)[o] = yv;
+  }
+  for (int i = nh_new - 1; i >= 1; --i) d.tn[(int64_t)i * d.ld + c] = d.tn[(int64_t)(i - 1) * d.ld + c];
+  d.tn[c] = d.log_t[(int64_t)(m - 1) * d.ld + c];
+  d.nh[c] = nh_new;
+}
+
+// One backward step at segment position j: block = one cell, one warp per
+// cotangent.  The slot holds the factors of M_m in elimination order (unit L,
+// U with inverse pivots on the diagonal), so M_m^T = U^T L^T is solved as a
+// forward sweep over the rows of U followed by a backward sweep over the rows
+// of L, each row scattering its contribution.
+__global__ void adj_step_kernel(Dev d, AdjDev a, int j) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t c = blockIdx.x;
+  const int m = seg_step(a, c, j);
+  if (!m) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int n = d.n, n_r = d.n_r, ldm = d.ldm;
+  double* Rs = reinterpret_cast<double*>(smem_raw);  // [n_r] reaction rates at y_m
+  double* xs = Rs + n_r + (size_t)warp * 2 * n;      // this warp's vector, elimination order
+  double* ls = xs + n;                               // lambda_m in species order
+  const double* ym = a.seg_y + (int64_t)j * n * a.lda;
+  for (int r = tid; r < n_r; r += blockDim.x) {
+    const int2 rc = __ldg(d.reac + r);
+    double v = a.kc[c * n_r + r] * ym[(int64_t)rc.x * a.lda + c];
+    if (rc.y >= 0) v *= ym[(int64_t)rc.y * a.lda + c];
+    Rs[r] = v;
+  }
+  __syncthreads();
+  const double h = a.seg_h[(int64_t)j * a.lda + c];
+  const double inv_a0 = 1.0 / a.seg_alpha[((int64_t)j * (QMAX + 1)) * a.lda + c];
+  const int N = a.N[c];
+  const int slot = m % kRing;
+  const double* A = slot_lu(d, a, j, c);
+  for (int v = warp; v < a.n_cot; v += nwarps) {
+    for (int s = lane; s < n; s += 32) {
+      double b = m == N ? a.cot[((int64_t)v * n + s) * a.ldu + c] : 0.0;
+      for (int dd = 1; dd <= QMAX && m + dd <= N; ++dd) {
+        const int sl = (m + dd) % kRing;
+        if (a.ring_q[(int64_t)sl * a.lda + c] >= dd)
+          b -= a.ring_alpha[((int64_t)sl * (QMAX + 1) + dd) * a.lda + c] *
+               a.lam[(((int64_t)sl * a.n_cot + v) * n + s) * a.lda + c];
+      }
+      xs[__ldg(d.iperm + s)] = b * inv_a0;
+    }
+    __syncwarp();
+    // U^T: u_k = x_k / u_kk, then x_j -= u_kj u_k over row k of U
+    for (int kk = 0; kk < n; ++kk) {
+      const double uk = xs[kk] * A[(int64_t)kk * ldm + kk];
+      __syncwarp();
+      if (lane == 0) xs[kk] = uk;
+      const double* Ak = A + (int64_t)kk * ldm;
+      const int p1 = __ldg(d.uptr + kk + 1);
+      for (int p = __ldg(d.uptr + kk) + lane; p < p1; p += 32) {
+        const int jj = __ldg(d.uidx + p);
+        xs[jj] -= Ak[jj] * uk;
+      }
+      __syncwarp();
+    }
+    // L^T (unit): v_i is final once the rows below it are done; x_k -= l_ik v_i
+    for (int ii = n - 1; ii > 0; --ii) {
+      const double vi = xs[ii];
+      const double* Ai = A + (int64_t)ii * ldm;
+      const int p1 = __ldg(d.lrptr + ii + 1);
+      for (int p = __ldg(d.lrptr + ii) + lane; p < p1; p += 32) {
+        const int kk = __ldg(d.lridx + p);
+        xs[kk] -= Ai[kk] * vi;
+      }
+      __syncwarp();
+    }
+    for (int s = lane; s < n; s += 32) {
+      const double lv = xs[__ldg(d.iperm + s)];
+      ls[s] = lv;
+      a.lam[(((int64_t)slot * a.n_cot + v) * n + s) * a.lda + c] = lv;
+    }
+    __syncwarp();
+    double* gv = a.g + (c * a.n_cot + v) * n_r;
+    for (int r = lane; r < n_r; r += 32) {
+      double w = 0.0;
+      const int p1 = __ldg(d.sc_ptr + r + 1);
+      for (int p = __ldg(d.sc_ptr + r); p < p1; ++p) {
+        const uint32_t e = __ldg(d.sc_ent + p);
+        w = fma((double)(int8_t)(e >> 24), ls[e & 0xFFFFFFu], w);
+      }
+      gv[r] = fma(h * Rs[r], w, gv[r]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (tid == 0) a.ring_q[(int64_t)slot * a.lda + c] = a.seg_q[(int64_t)j * a.lda + c];
+  if (tid <= QMAX)
+    a.ring_alpha[((int64_t)slot * (QMAX + 1) + tid) * a.lda + c] =
+        a.seg_alpha[((int64_t)j * (QMAX + 1) + tid) * a.lda + c];
+}
+
+// Gradient out as [n_cot][n_r][ldg] (cells fastest), per-cell status, and the
+// number of cells without a usable result in counters[2].
+__global__ void adj_out_kernel(Dev d, AdjDev a, double* __restrict__ out, int64_t ldg, int* __restrict__ astat_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  for (int v = 0; v < a.n_cot; ++v)
+    for (int r = 0; r < d.n_r; ++r)
+      out[((int64_t)v * d.n_r + r) * ldg + c] = a.g[(c * a.n_cot + v) * d.n_r + r];
+  const int s = a.astat[c];
+  if (astat_out) astat_out[c] = s;
+  if (s) atomicAdd(&d.counters[2], 1);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1044,7 +1349,8 @@ struct sm_state {
   int64_t cap = 0, C = 0, ld = 0;
   double t_end = 0.0;
   Dev d{};
-  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, l21;
+  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, l21, rec_d, rec_i;
+  DevArray adj_d, adj_i, adj_lu;   // sm_adjoint workspace, grown on demand
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int* h_counters = nullptr;  // pinned
@@ -1078,6 +1384,7 @@ extern "C" void sm_opts_default(sm_opts* o) {
   o->use_graph = 1;
   o->attempts_per_sync = 8;
   o->timing_kind = SM_TIME_NONE;
+  o->record_steps = 0;
 }
 
 namespace {
@@ -1099,7 +1406,7 @@ bool opts_ok(const sm_opts& o) {
          o.eta_keep >= 1.0 && o.q_max >= 1 && o.q_max <= QMAX && o.max_steps >= 1 && o.j_age_max >= 1 &&
          o.newton_max >= 1 && o.newton_max <= 8 && o.max_conv_fails >= 1 &&
          (o.precision == SM_PREC_FP64 || o.precision == SM_PREC_MIXED) && o.attempts_per_sync >= 1 &&
-         o.timing_kind >= SM_TIME_NONE && o.timing_kind <= SM_TIME_FINISH;
+         o.timing_kind >= SM_TIME_NONE && o.timing_kind <= SM_TIME_FINISH && o.record_steps >= 0;
 }
 
 void free_state(sm_state* st) {
@@ -1114,6 +1421,11 @@ void free_state(sm_state* st) {
   st->counters.release();
   st->scratch.release();
   st->l21.release();
+  st->rec_d.release();
+  st->rec_i.release();
+  st->adj_d.release();
+  st->adj_i.release();
+  st->adj_lu.release();
   if (st->h_counters) cudaFreeHost(st->h_counters);
   if (st->ev_in) cudaEventDestroy(st->ev_in);
   if (st->ev_out) cudaEventDestroy(st->ev_out);
@@ -1181,7 +1493,7 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
     if (r != SM_OK) return r;
     if ((r = time_mark(st, SM_TIME_RHS, false, s)) != SM_OK) return r;
     if ((r = time_mark(st, SM_TIME_SOLVE, true, s)) != SM_OK) return r;
-    solve_update_kernel<T><<<blocks(d.C, kSolveWarps), 32 * kSolveWarps, smem, s>>>(d);
+    solve_update_kernel<T><<<blocks(d.C, kSolveWarps), 32 * kSolveWarps, smem, s>>>(d, F_NEWTON, F_NEWTON);
     if ((r = time_mark(st, SM_TIME_SOLVE, false, s)) != SM_OK) return r;
   }
   if ((r = time_mark(st, SM_TIME_FINISH, true, s)) != SM_OK) return r;
@@ -1283,6 +1595,119 @@ sm_status join_out(sm_state* st, void* stream) {
   return SM_OK;
 }
 
+
+// The per-cell views of cells [c0, c0 + Cc) as a state of Cc cells.
+Dev shift_cells(const Dev& d0, int64_t c0, int64_t Cc) {
+  Dev d = d0;
+  d.C = Cc;
+  auto sh = [c0](auto*& p) {
+    if (p) p += c0;
+  };
+  sh(d.t); sh(d.h); sh(d.gam); sh(d.gam_J); sh(d.crate); sh(d.dprev); sh(d.tn); sh(d.alpha);
+  sh(d.q); sh(d.nh); sh(d.n_at_q); sh(d.j_age); sh(d.flags); sh(d.crej); sh(d.ccf); sh(d.status);
+  sh(d.m_it); sh(d.steps); sh(d.rejects); sh(d.conv_fails); sh(d.newton_iters); sh(d.jac_evals);
+  sh(d.Y); sh(d.ypred); sh(d.y); sh(d.psi); sh(d.f); sh(d.f0); sh(d.eprev); sh(d.w); sh(d.wf);
+  sh(d.log_t); sh(d.log_h); sh(d.log_q); sh(d.ck_Y); sh(d.ck_t); sh(d.ck_nh);
+  return d;
+}
+
+// One pass of the reverse sweep over cells [c0, c0 + Cp); adds the number of
+// cells without a usable result to *bad.
+sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const double* k, int64_t ldk,
+                       const double* cot, int n_cot, double* grad, int32_t* astat, int warps, size_t smem,
+                       int64_t* bad) {
+  const sm_net* net = st->net;
+  const int n = st->d.n, n_r = st->d.n_r;
+  cudaStream_t s = st->s;
+  Dev dd = shift_cells(st->d, c0, Cp);
+  dd.mixed = 0;
+  dd.newton_tol = kReplayTol;
+  dd.newton_max = kReplayIters;
+  double* ad = st->adj_d.as<double>();
+  int* ai = st->adj_i.as<int>();
+  dd.jac_evals = ai + (4 + kCkpt + kRing) * lda;   // replay counters stay out of the run's statistics
+  dd.newton_iters = dd.jac_evals + lda;
+  AdjDev a{};
+  a.n_cot = n_cot;
+  a.run_tol = st->d.newton_tol;
+  a.lda = lda;
+  a.N = ai; a.K = ai + lda; a.seg = ai + 2 * lda; a.astat = ai + 3 * lda;
+  a.seg_q = ai + 4 * lda; a.ring_q = a.seg_q + kCkpt * lda;
+  a.seg_y = ad;
+  a.seg_h = a.seg_y + (int64_t)kCkpt * n * lda;
+  a.seg_alpha = a.seg_h + kCkpt * lda;
+  a.ring_alpha = a.seg_alpha + (int64_t)kCkpt * (QMAX + 1) * lda;
+  a.lam = a.ring_alpha + (int64_t)kRing * (QMAX + 1) * lda;
+  a.kc = a.lam + (int64_t)kRing * n_cot * n * lda;
+  a.g = a.kc + Cp * n_r;
+  a.slots = st->adj_lu.as<double>();
+  a.cot = cot + c0;
+  a.ldu = ldk;
+  const double* kp = k + c0;
+  double* scratch = st->scratch.as<double>() + c0;
+  auto slot_dev = [&](int j) {
+    Dev x = dd;
+    x.lu = a.slots + (int64_t)j * Cp * dd.lu_stride;
+    return x;
+  };
+  auto refresh_at = [&](int j, int need_flag) -> sm_status {
+    SM_TRY_CUDA(cudaMemsetAsync(dd.counters, 0, sizeof(int), s));
+    adj_list_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, need_flag);
+    refresh_kernel<double><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(slot_dev(j), kp, ldk, st->plan);
+    st->launches += 2;
+    return SM_OK;
+  };
+  sm_status r;
+  SM_TRY_CUDA(cudaMemsetAsync(dd.counters, 0, 4 * sizeof(int), s));
+  adj_setup_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, kp, ldk);
+  SM_TRY_CUDA(cudaGetLastError());
+  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, dd.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SM_TRY_CUDA(cudaStreamSynchronize(s));
+  const int Kmax = st->h_counters[3];
+  st->launches += 1;
+  const size_t solve_smem = sizeof(double) * (size_t)kSolveWarps * ((n + 3) / 4 * 4);
+  for (int rs = 0; rs < Kmax; ++rs) {
+    seg_restore_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, rs);
+    st->launches += 1;
+    for (int j = 0; j < kCkpt; ++j) {
+      rpredict_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
+      st->launches += 1;
+      // Newton matrix: the factors at y_{m-1} (slot j - 1), or, for the cells
+      // flagged F_REFRESH, fresh ones at the predictor in slot j (replaced by
+      // the factors at y_m once the step is solved)
+      if ((r = refresh_at(j, F_REFRESH)) != SM_OK) return r;
+      const Dev d_old = slot_dev(j > 0 ? j - 1 : 0), d_new = slot_dev(j);
+      const int need = F_NEWTON | F_REFRESH;
+      for (int it = 0; it < kReplayIters; ++it) {
+        r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
+        if (r != SM_OK) return r;
+        if (j > 0) {
+          solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_old, need, F_NEWTON);
+          st->launches += 1;
+        }
+        solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_new, need, need);
+        st->launches += 3;
+      }
+      rcommit_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
+      st->launches += 1;
+      if ((r = refresh_at(j, 0)) != SM_OK) return r;
+    }
+    for (int j = kCkpt - 1; j >= 0; --j) {
+      adj_step_kernel<<<(unsigned)Cp, 32 * warps, smem, s>>>(dd, a, j);
+      st->launches += 1;
+    }
+    SM_TRY_CUDA(cudaGetLastError());
+  }
+  SM_TRY_CUDA(cudaMemsetAsync(dd.counters + 2, 0, sizeof(int), s));
+  adj_out_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, grad + c0, ldk, astat ? astat + c0 : nullptr);
+  SM_TRY_CUDA(cudaGetLastError());
+  st->launches += 1;
+  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, dd.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SM_TRY_CUDA(cudaStreamSynchronize(s));
+  *bad += st->h_counters[2];
+  return SM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1369,8 +1794,25 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.u12off = lu.d_u12off.as<int>();
   d.lrhk = lu.d_lrhk.as<int>();
   d.jt_slot = net->d_jt_slot.as<int2>(); d.reac = net->d_reac.as<int2>();
+  d.sc_ptr = net->d_sc_ptr.as<int>(); d.sc_ent = net->d_sc_ent.as<uint32_t>();
   d.jp_ptr = net->d_jp_ptr.as<int>(); d.jt_ptr = net->d_jt_ptr.as<int>();
   d.jt_word = net->d_jt_word.as<int2>(); d.jpos = lu.d_jpos.as<int>();
+  d.record = o.record_steps > 0 ? o.record_steps : 0;
+  if (d.record) {
+    const int64_t R = d.record, K = R / kCkpt + 1;
+    if ((r = st->rec_d.ensure(sizeof(double) * (size_t)(2 * R * ld + K * (QMAX + 1) * (int64_t)n * ld +
+                                                        K * (QMAX + 1) * ld))) != SM_OK)
+      return fail(r);
+    if ((r = st->rec_i.ensure(sizeof(int) * (size_t)(R * ld + K * ld))) != SM_OK) return fail(r);
+    double* rd = st->rec_d.as<double>();
+    d.log_t = rd;
+    d.log_h = rd + R * ld;
+    d.ck_Y = rd + 2 * R * ld;
+    d.ck_t = d.ck_Y + K * (QMAX + 1) * (int64_t)n * ld;
+    int* ri = st->rec_i.as<int>();
+    d.log_q = ri;
+    d.ck_nh = ri + R * ld;
+  }
   if (cudaStreamCreateWithFlags(&st->s, cudaStreamNonBlocking) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
@@ -1410,10 +1852,13 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   const size_t rsm = st->plan.bytes;
 
   if ((int64_t)rsm > smem_max) return fail(SM_ENOTSUP);
+  // the attribute is a per-kernel cap shared by every state: set it to the
+  // device limit so that a later state with a smaller plan cannot lower it
+  // below what an earlier state launches with
   if (d.mixed) {
-    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   } else {
-    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    SM_TRY_CUDA(cudaFuncSetAttribute(refresh_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   }
   int per_sm = 0;
   if (d.mixed) {
@@ -1442,7 +1887,8 @@ sm_status sm_state_free(sm_state* st) {
 sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
   if (!st || !bytes) return SM_EINVAL;
   *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->list.bytes +
-           st->counters.bytes + st->scratch.bytes + st->l21.bytes;
+           st->counters.bytes + st->scratch.bytes + st->l21.bytes + st->rec_d.bytes + st->rec_i.bytes + st->adj_d.bytes + st->adj_i.bytes +
+           st->adj_lu.bytes;
   return SM_OK;
 }
 
@@ -1519,6 +1965,62 @@ sm_status sm_integrate(sm_state* st, int64_t C, const double* d_k, double* d_y, 
   if ((r = join_out(st, stream)) != SM_OK) return r;
   // a cell that did not reach t_end makes the call partial
   return (running > 0 || failed > 0) ? SM_EPARTIAL : SM_OK;
+}
+
+sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, int32_t* d_q, int64_t ld,
+                         void* stream) {
+  if (!st || st->C < 1 || m_max < 1 || m_max > st->d.record || !ld_ok(st->C, ld) || !d_t || !d_h || !d_q)
+    return SM_EINVAL;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  const Dev& d = st->d;
+  SM_TRY_CUDA(cudaMemcpy2DAsync(d_t, ld * sizeof(double), d.log_t, d.ld * sizeof(double), st->C * sizeof(double),
+                                m_max, cudaMemcpyDeviceToDevice, st->s));
+  SM_TRY_CUDA(cudaMemcpy2DAsync(d_h, ld * sizeof(double), d.log_h, d.ld * sizeof(double), st->C * sizeof(double),
+                                m_max, cudaMemcpyDeviceToDevice, st->s));
+  SM_TRY_CUDA(cudaMemcpy2DAsync(d_q, ld * sizeof(int32_t), d.log_q, d.ld * sizeof(int), st->C * sizeof(int32_t),
+                                m_max, cudaMemcpyDeviceToDevice, st->s));
+  return join_out(st, stream);
+}
+
+sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* d_cot, int32_t n_cot,
+                     double* d_grad, int32_t* d_astat, int64_t cells_per_pass, void* stream) {
+  if (!st || !d_k || !d_cot || !d_grad || n_cot < 1 || n_cot > SM_ADJ_MAX_COT || st->C < 1 ||
+      !ld_ok(st->C, ld) || cells_per_pass < 0 || st->d.record < 1)
+    return SM_EINVAL;
+  if (st->d.mixed) return SM_ENOTSUP;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  const int64_t C = st->C;
+  const int n = st->d.n, n_r = st->d.n_r;
+  int64_t Cc = cells_per_pass > 0 ? std::min<int64_t>(cells_per_pass, C) : C;
+  if (Cc < C) Cc = std::min<int64_t>(C, (Cc + 31) / 32 * 32);  // passes start on 32-cell boundaries
+  const int64_t lda = (Cc + 31) / 32 * 32;
+  const size_t nd = (size_t)kCkpt * n * lda + (size_t)kCkpt * lda + (size_t)kCkpt * (QMAX + 1) * lda +
+                    (size_t)kRing * (QMAX + 1) * lda + (size_t)kRing * n_cot * n * lda + (size_t)Cc * n_r +
+                    (size_t)Cc * n_cot * n_r;
+  const size_t ni = (size_t)(4 + kCkpt + kRing + 2) * lda;
+  if ((r = st->adj_d.ensure(sizeof(double) * nd)) != SM_OK) return r;
+  if ((r = st->adj_i.ensure(sizeof(int) * ni)) != SM_OK) return r;
+  if ((r = st->adj_lu.ensure(sizeof(double) * (size_t)kCkpt * Cc * st->d.lu_stride)) != SM_OK) return r;
+  const int warps = std::min(n_cot, 8);
+  const size_t smem = sizeof(double) * ((size_t)n_r + (size_t)warps * 2 * n);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, st->net->device);
+  if (smem > (size_t)smem_max) return SM_ENOTSUP;
+  SM_TRY_CUDA(cudaFuncSetAttribute(adj_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  int64_t bad = 0;
+  for (int64_t c0 = 0; c0 < C; c0 += Cc) {
+    const int64_t Cp = std::min(Cc, C - c0);
+    r = adjoint_pass(st, c0, Cp, lda, d_k, ld, d_cot, n_cot, d_grad, d_astat, warps, smem, &bad);
+    if (r != SM_OK) return r;
+  }
+  if ((r = join_out(st, stream)) != SM_OK) return r;
+  return bad > 0 ? SM_EPARTIAL : SM_OK;
 }
 
 }  // extern "C"

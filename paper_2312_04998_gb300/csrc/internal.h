@@ -105,6 +105,7 @@ struct sm_net {
   DevArray d_rate;        // RatePar per reaction: (log alpha | alpha, beta, gamma, class)
   DevArray d_jp_ptr, d_jt_ptr, d_jt_word;  // Jacobian gather lists
   DevArray d_jt_slot;                      // (reaction | coef << 24, reactant slot) per term
+  DevArray d_sc_ptr, d_sc_ent;             // S by columns: pointers and (species | coef << 24)
   std::vector<int32_t> jchunk;             // J entries per gather chunk (balanced by terms)
   DevArray d_jchunk;
   DevArray d_status;      // int32 device status word

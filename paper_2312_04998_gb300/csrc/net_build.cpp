@@ -598,6 +598,12 @@ sm_status net_upload(sm_net* net) {
     words[2 * t] = (int32_t)pack(net->jt_rx[t], net->jt_coef[t]);
     words[2 * t + 1] = net->jt_partner[t];
   }
+  {
+    std::vector<uint32_t> ent(net->s_row.size());
+    for (size_t p = 0; p < ent.size(); ++p) ent[p] = pack(net->s_row[p], net->s_coef[p]);
+    if ((st = net->d_sc_ptr.upload(net->s_colptr.data(), net->s_colptr.size() * 4)) != SM_OK) return st;
+    if ((st = net->d_sc_ent.upload(ent.data(), ent.size() * 4)) != SM_OK) return st;
+  }
   if ((st = net->d_jp_ptr.upload(net->jp_ptr.data(), net->jp_ptr.size() * 4)) != SM_OK) return st;
   if ((st = net->d_jt_ptr.upload(net->jt_ptr.data(), net->jt_ptr.size() * 4)) != SM_OK) return st;
   if ((st = net->d_jt_word.upload(words.data(), words.size() * 4)) != SM_OK) return st;
