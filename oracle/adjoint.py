@@ -89,8 +89,11 @@ def _alphas_all(steps):
     return res
 
 
-def adjoint(desc, k, ys, steps, cot, S=None):
-    """dPhi/d log k (one row per cotangent) for Phi = cot^T y_N."""
+def adjoint(desc, k, ys, steps, cot, S=None, with_y0=False):
+    """dPhi/d log k (one row per cotangent) for Phi = cot^T y_N; with
+    `with_y0` also dPhi/dy_0, the same backward recursion taken one step
+    further: y_0 enters the equations of the steps m' with m' <= q_{m'}
+    through alpha_{m'}^{m'} y_0, so dPhi/dy_0 = -sum_{m'} alpha_{m'}^{m'} lambda_{m'}."""
     if S is None:
         S = stoichiometry(desc)
     k = np.asarray(k, dtype=float)
@@ -111,7 +114,32 @@ def adjoint(desc, k, ys, steps, cot, S=None):
         lam[m] = sla.solve(A.T, b)
         R = reaction_rates(desc, k, ys[m])
         grad += h * (S.T @ lam[m]).T * R[None, :]
-    return grad
+    if not with_y0:
+        return grad
+    g0 = np.zeros((n, cot.shape[0]))
+    for mp in range(1, min(N, 5) + 1):
+        if mp <= steps[mp - 1][2]:
+            g0 -= alphas[mp - 1][mp] * lam[mp]
+    return grad, g0.T
+
+
+def forward_sensitivity_y0(desc, k, ys, steps, S=None):
+    """dy_N / dy_0 (n_s x n_s) through the frozen map: the tangent recursion of
+    `forward_sensitivity` with the identity as initial tangent and no source."""
+    if S is None:
+        S = stoichiometry(desc)
+    k = np.asarray(k, dtype=float)
+    n = desc.n_s
+    alphas = _alphas_all(steps)
+    sens = [np.eye(n)]
+    for m, (t_new, h, q) in enumerate(steps, start=1):
+        a = alphas[m - 1]
+        rhs = np.zeros((n, n))
+        for i in range(1, q + 1):
+            rhs -= a[i] * sens[m - i]
+        A = a[0] * np.eye(n) - h * jacobian(desc, k, ys[m], S)
+        sens.append(np.linalg.solve(A, rhs))
+    return sens[-1]
 
 
 def forward_sensitivity(desc, k, ys, steps, S=None):
