@@ -319,6 +319,9 @@ sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, 
  * d_k     = the k'[n_r][ld] the recorded run was integrated with (device);
  * d_cot   = c[n_cot][n_s][ld] (device), the weights of y_N for each Phi;
  * d_grad  = out[n_cot][n_r][ld] (device): dPhi_v / d log k_j per cell;
+ * d_grad_y0 = out[n_cot][n_s][ld] (device, may be NULL): dPhi_v / dy_0, the
+ *           recursion continued to the initial state, which enters the first
+ *           steps' equations through alpha_{m'}^{m'} y_0 (m' <= q_{m'});
  * d_astat = per-cell status (device, C entries, may be NULL): 0 ok, 1 no
  *           usable record (the cell did not finish with SM_CELL_OK or took
  *           more than opts.record_steps steps; its gradient is 0), 2 a
@@ -340,7 +343,21 @@ sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, 
  * SM_EPARTIAL if any cell's d_astat is not 0.  Synchronises the host with the
  * state's stream once per pass. */
 sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* d_cot, int32_t n_cot,
-                     double* d_grad, int32_t* d_astat, int64_t cells_per_pass, void* stream);
+                     double* d_grad, double* d_grad_y0, int32_t* d_astat, int64_t cells_per_pass,
+                     void* stream);
+
+/* Frozen-step replay: re-solves the recorded run's accepted steps (same t_m,
+ * h_m, q_m) from its recorded initial state with other rate coefficients d_k
+ * (k'[n_r][ld], device) and writes y_N to d_y (x[n_s][ld], device; NaN for
+ * cells without a usable record).  Each implicit step is solved by Newton to
+ * 1e-4 in the run's WRMS norm, with the Newton matrix refreshed when h/alpha_0
+ * moves by more than opts.gamma_tol and every SM_CHECKPOINT_EVERY steps.  This
+ * is the map sm_adjoint differentiates, so central differences of it check
+ * the adjoint.  d_astat, cells_per_pass, the errors and the effect on the
+ * state's working vectors are those of sm_adjoint (no factor slots are used:
+ * the workspace is the cotangent-free part). */
+sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, int32_t* d_astat,
+                    int64_t cells_per_pass, void* stream);
 
 /* Wait for all work on `stream` and report (and clear) any error a kernel of
  * this network wrote to its device status word. */

@@ -101,7 +101,9 @@ _SIGS = [
     ("sm_state_steps", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                     ct.c_int64, ct.c_void_p]),
     ("sm_adjoint", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int32,
-                                ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+                                ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    ("sm_replay", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p,
+                               ct.c_int64, ct.c_void_p]),
 ]
 ADJ_MAX_COT = 64
 
@@ -264,6 +266,7 @@ class State:
                "sm_state_create")
         self.h = h
         self.cells = cells
+        self.generation = 0   # counts integrations (autograd checks its record is current)
 
     def close(self):
         if getattr(self, "h", None):
@@ -296,6 +299,7 @@ class State:
         Returns the status code (SM_OK or SM_EPARTIAL)."""
         C = y.shape[1] if C is None else C
         ld = self.net._ld(k, y)
+        self.generation += 1
         code = lib().sm_integrate(self.h, int(C), _dptr(k), _dptr(y), int(ld), float(t_end),
                                   _dptr(stats) if stats is not None else None, _stream(y.device))
         if code == SM_EPARTIAL and allow_partial:
@@ -305,6 +309,7 @@ class State:
 
     def init(self, k, y, t_end, C=None):
         C = y.shape[1] if C is None else C
+        self.generation += 1
         _check(lib().sm_state_init(self.h, int(C), _dptr(k), _dptr(y), int(self.net._ld(k, y)),
                                    float(t_end), _stream(y.device)), "sm_state_init")
 
@@ -337,19 +342,34 @@ class State:
                "sm_state_steps")
         return t, h, q
 
-    def adjoint(self, k, cot, grad, astat=None, cells_per_pass=0, allow_partial=True):
+    def adjoint(self, k, cot, grad, astat=None, cells_per_pass=0, allow_partial=True, grad_y0=None):
         """Reverse sweep of the last recorded run: cot [n_cot][n_s][ld] ->
-        grad [n_cot][n_r][ld] = dPhi/dlog k per cell (device float64 tensors,
-        same ld as k).  astat: optional device int32 tensor of C entries.
+        grad [n_cot][n_r][ld] = dPhi/dlog k per cell and, if given, grad_y0
+        [n_cot][n_s][ld] = dPhi/dy_0 (device float64 tensors, same ld as k).
+        astat: optional device int32 tensor of C entries.
         Returns SM_OK or SM_EPARTIAL."""
         ld = int(k.stride(0))
         assert cot.dim() == 3 and cot.stride(1) == ld and grad.stride(1) == ld
+        assert grad_y0 is None or grad_y0.stride(1) == ld
         code = lib().sm_adjoint(self.h, _dptr(k), ld, _dptr(cot), int(cot.shape[0]), _dptr(grad),
+                                _dptr(grad_y0) if grad_y0 is not None else None,
                                 _dptr(astat) if astat is not None else None, int(cells_per_pass),
                                 _stream(k.device))
         if code == SM_EPARTIAL and allow_partial:
             return code
         _check(code, "sm_adjoint")
+        return code
+
+    def replay(self, k, y, astat=None, cells_per_pass=0, allow_partial=True):
+        """Frozen-step replay of the last recorded run with rate coefficients k;
+        y [n_s][ld] receives y_N.  Returns SM_OK or SM_EPARTIAL."""
+        ld = int(k.stride(0))
+        assert y.stride(0) == ld
+        code = lib().sm_replay(self.h, _dptr(k), ld, _dptr(y), _dptr(astat) if astat is not None else None,
+                               int(cells_per_pass), _stream(k.device))
+        if code == SM_EPARTIAL and allow_partial:
+            return code
+        _check(code, "sm_replay")
         return code
 
 

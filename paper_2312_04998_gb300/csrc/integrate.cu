@@ -1120,16 +1120,18 @@ __global__ void adj_setup_kernel(Dev d, AdjDev a, const double* __restrict__ k, 
   a.K[c] = K;
   a.astat[c] = ok ? 0 : 1;
   atomicMax(&d.counters[3], K);
+  atomicMax(&d.counters[1], ok ? N : 0);
   for (int j = 0; j < d.n_r; ++j) a.kc[c * d.n_r + j] = k[(int64_t)j * ldk + c];
   for (int64_t i = 0; i < (int64_t)a.n_cot * d.n_r; ++i) a.g[c * a.n_cot * d.n_r + i] = 0.0;
   for (int i = 0; i < kRing; ++i) a.ring_q[(int64_t)i * a.lda + c] = 0;
 }
 
-// Restores the step history stored before segment K - 1 - rs.
+// Restores the step history stored before segment K - 1 - rs (rs >= 0), or
+// before segment 0 for every cell (rs < 0: a replay from the start).
 __global__ void seg_restore_kernel(Dev d, AdjDev a, int rs) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.C) return;
-  const int sg = a.astat[c] == 0 ? a.K[c] - 1 - rs : -1;
+  const int sg = a.astat[c] == 0 ? (rs >= 0 ? a.K[c] - 1 - rs : 0) : -1;
   a.seg[c] = sg;
   if (sg < 0) return;
   const int nh = d.ck_nh[(int64_t)sg * d.ld + c];
@@ -1150,8 +1152,9 @@ __device__ __forceinline__ int seg_step(const AdjDev& a, int64_t c, int j) {
   return m <= a.N[c] ? m : 0;
 }
 
-// Predictor, BDF coefficients and Newton set-up of frozen step m.
-__global__ void rpredict_kernel(Dev d, AdjDev a, int j) {
+// Predictor, BDF coefficients and Newton set-up of frozen step m; with
+// `store` the step's h, q and alpha are kept for the backward pass.
+__global__ void rpredict_kernel(Dev d, AdjDev a, int j, int store) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.C) return;
   const int m = seg_step(a, c, j);
@@ -1173,14 +1176,16 @@ __global__ void rpredict_kernel(Dev d, AdjDev a, int j) {
   for (int i = 0; i <= QMAX; ++i) {
     const double v = i <= q ? al[i] : 0.0;
     d.alpha[(int64_t)i * d.ld + c] = v;
-    a.seg_alpha[((int64_t)j * (QMAX + 1) + i) * a.lda + c] = v;
+    if (store) a.seg_alpha[((int64_t)j * (QMAX + 1) + i) * a.lda + c] = v;
   }
-  a.seg_h[(int64_t)j * a.lda + c] = h;
-  a.seg_q[(int64_t)j * a.lda + c] = q;
-  // the factors at y_{m-1} serve as Newton matrix unless gamma moved too far
-  // from theirs (the integrator's own refresh rule); the segment's first step
-  // always starts from fresh factors at the predictor
-  const bool fresh = j == 0 || fabs(h / al[0] / d.gam_J[c] - 1.0) > d.gamma_tol;
+  if (store) {
+    a.seg_h[(int64_t)j * a.lda + c] = h;
+    a.seg_q[(int64_t)j * a.lda + c] = q;
+  }
+  // the previous step's factors serve as Newton matrix unless gamma moved too
+  // far from theirs (the integrator's own refresh rule); every kCkpt-th step
+  // (each segment's first) starts from fresh factors at the predictor
+  const bool fresh = j % kCkpt == 0 || fabs(h / al[0] / d.gam_J[c] - 1.0) > d.gamma_tol;
   d.flags[c] = F_NEWTON | (fresh ? F_REFRESH : 0);
   d.m_it[c] = 0;
   d.dprev[c] = 0.0;
@@ -1212,9 +1217,27 @@ __global__ void adj_list_kernel(Dev d, AdjDev a, int j, int need_flag) {
   if (seg_step(a, c, j) && (d.flags[c] & need_flag) == need_flag) d.list[atomicAdd(&d.counters[0], 1)] = (int)c;
 }
 
+// Second chance for cells whose Newton iteration did not converge: restart
+// from the predictor with fresh factors (F_REFRESH); converged cells are
+// taken out of the Newton set.
+__global__ void rretry_kernel(Dev d, AdjDev a, int j) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  if (!seg_step(a, c, j)) return;
+  if (d.flags[c] & F_CONV) {
+    d.flags[c] = F_CONV;
+    return;
+  }
+  d.flags[c] = F_NEWTON | F_REFRESH;
+  d.m_it[c] = 0;
+  d.dprev[c] = 0.0;
+  d.crate[c] = 1.0;
+  for (int s = 0; s < d.n; ++s) d.y[(int64_t)s * d.ld + c] = d.ypred[(int64_t)s * d.ld + c];
+}
+
 // Keeps the solved state for the backward pass and shifts the history; the
 // state also becomes the point at which the next refresh evaluates J.
-__global__ void rcommit_kernel(Dev d, AdjDev a, int j) {
+__global__ void rcommit_kernel(Dev d, AdjDev a, int j, int store) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.C) return;
   const int m = seg_step(a, c, j);
@@ -1226,8 +1249,10 @@ __global__ void rcommit_kernel(Dev d, AdjDev a, int j) {
   for (int s = 0; s < d.n; ++s) {
     const int64_t o = (int64_t)s * d.ld + c;
     const double yv = d.y[o];
-    a.seg_y[((int64_t)j * d.n + s) * a.lda + c] = yv;
-    d.ypred[o] = yv;
+    if (store) {
+      a.seg_y[((int64_t)j * d.n + s) * a.lda + c] = yv;
+      d.ypred[o] = yv;
+    }
     for (int i = nh_new - 1; i >= 1; --i) Yh(d, i)[o] = Yh(d, i - 1)[o];
     Yh(d, 0)[o] = yv;
   }
@@ -1334,6 +1359,38 @@ __global__ void adj_out_kernel(Dev d, AdjDev a, double* __restrict__ out, int64_
     for (int r = 0; r < d.n_r; ++r)
       out[((int64_t)v * d.n_r + r) * ldg + c] = a.g[(c * a.n_cot + v) * d.n_r + r];
   const int s = a.astat[c];
+  if (astat_out) astat_out[c] = s;
+  if (s) atomicAdd(&d.counters[2], 1);
+}
+
+// dPhi/dy_0 = -sum_{m'} alpha_{m'}^{m'} lambda_{m'} over the first steps with
+// q_{m'} >= m' (their lambdas are still in the ring once segment 0 is done),
+// as out[n_cot][n][ldg]; 0 for cells without a usable result.
+__global__ void adj_y0_kernel(Dev d, AdjDev a, double* __restrict__ out, int64_t ldg) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const bool ok = a.astat[c] == 0;
+  const int N = a.N[c];
+  for (int v = 0; v < a.n_cot; ++v)
+    for (int s = 0; s < d.n; ++s) {
+      double g = 0.0;
+      for (int mp = 1; ok && mp <= QMAX && mp <= N; ++mp) {
+        const int sl = mp % kRing;
+        if (a.ring_q[(int64_t)sl * a.lda + c] >= mp)
+          g -= a.ring_alpha[((int64_t)sl * (QMAX + 1) + mp) * a.lda + c] *
+               a.lam[(((int64_t)sl * a.n_cot + v) * d.n + s) * a.lda + c];
+      }
+      out[((int64_t)v * d.n + s) * ldg + c] = g;
+    }
+}
+
+// Replay result: y_N of replayed cells, NaN for the others.
+__global__ void replay_out_kernel(Dev d, AdjDev a, double* __restrict__ yout, int64_t ldu,
+                                  int* __restrict__ astat_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int s = a.astat[c];
+  for (int i = 0; i < d.n; ++i) yout[(int64_t)i * ldu + c] = s == 0 ? Yh(d, 0)[(int64_t)i * d.ld + c] : NAN;
   if (astat_out) astat_out[c] = s;
   if (s) atomicAdd(&d.counters[2], 1);
 }
@@ -1611,12 +1668,12 @@ Dev shift_cells(const Dev& d0, int64_t c0, int64_t Cc) {
   return d;
 }
 
-// One pass of the reverse sweep over cells [c0, c0 + Cp); adds the number of
-// cells without a usable result to *bad.
-sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const double* k, int64_t ldk,
-                       const double* cot, int n_cot, double* grad, int32_t* astat, int warps, size_t smem,
-                       int64_t* bad) {
-  const sm_net* net = st->net;
+// Views of the pass [c0, c0 + Cp) for the reverse sweep and the replay: the
+// state shifted to the pass, Newton set to the replay tolerance, and the
+// adjoint workspace carved up.  Runs the per-cell set-up and returns the
+// largest segment count and step count of the pass.
+sm_status adj_prepare(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const double* k, int64_t ldk,
+                      const double* cot, int n_cot, Dev* dd_out, AdjDev* a_out, int* Kmax, int* Nmax) {
   const int n = st->d.n, n_r = st->d.n_r;
   cudaStream_t s = st->s;
   Dev dd = shift_cells(st->d, c0, Cp);
@@ -1641,8 +1698,42 @@ sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const 
   a.kc = a.lam + (int64_t)kRing * n_cot * n * lda;
   a.g = a.kc + Cp * n_r;
   a.slots = st->adj_lu.as<double>();
-  a.cot = cot + c0;
+  a.cot = cot ? cot + c0 : nullptr;
   a.ldu = ldk;
+  SM_TRY_CUDA(cudaMemsetAsync(dd.counters, 0, 4 * sizeof(int), s));
+  adj_setup_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, k + c0, ldk);
+  SM_TRY_CUDA(cudaGetLastError());
+  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, dd.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  SM_TRY_CUDA(cudaStreamSynchronize(s));
+  st->launches += 1;
+  *Kmax = st->h_counters[3];
+  *Nmax = st->h_counters[1];
+  *dd_out = dd;
+  *a_out = a;
+  return SM_OK;
+}
+
+// Number of cells without a usable result (counters[2], set by the output
+// kernels), added to *bad.
+sm_status adj_count_bad(sm_state* st, int64_t* bad) {
+  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, st->d.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st->s));
+  SM_TRY_CUDA(cudaStreamSynchronize(st->s));
+  *bad += st->h_counters[2];
+  return SM_OK;
+}
+
+// One pass of the reverse sweep over cells [c0, c0 + Cp); adds the number of
+// cells without a usable result to *bad.
+sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const double* k, int64_t ldk,
+                       const double* cot, int n_cot, double* grad, double* grad_y0, int32_t* astat, int warps,
+                       size_t smem, int64_t* bad) {
+  const sm_net* net = st->net;
+  cudaStream_t s = st->s;
+  Dev dd;
+  AdjDev a;
+  int Kmax = 0, Nmax = 0;
+  sm_status r = adj_prepare(st, c0, Cp, lda, k, ldk, cot, n_cot, &dd, &a, &Kmax, &Nmax);
+  if (r != SM_OK) return r;
   const double* kp = k + c0;
   double* scratch = st->scratch.as<double>() + c0;
   auto slot_dev = [&](int j) {
@@ -1657,38 +1748,36 @@ sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const 
     st->launches += 2;
     return SM_OK;
   };
-  sm_status r;
-  SM_TRY_CUDA(cudaMemsetAsync(dd.counters, 0, 4 * sizeof(int), s));
-  adj_setup_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, kp, ldk);
-  SM_TRY_CUDA(cudaGetLastError());
-  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, dd.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  SM_TRY_CUDA(cudaStreamSynchronize(s));
-  const int Kmax = st->h_counters[3];
-  st->launches += 1;
-  const size_t solve_smem = sizeof(double) * (size_t)kSolveWarps * ((n + 3) / 4 * 4);
+  const size_t solve_smem = sizeof(double) * (size_t)kSolveWarps * ((dd.n + 3) / 4 * 4);
   for (int rs = 0; rs < Kmax; ++rs) {
     seg_restore_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, rs);
     st->launches += 1;
     for (int j = 0; j < kCkpt; ++j) {
-      rpredict_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
+      rpredict_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, 1);
       st->launches += 1;
       // Newton matrix: the factors at y_{m-1} (slot j - 1), or, for the cells
       // flagged F_REFRESH, fresh ones at the predictor in slot j (replaced by
       // the factors at y_m once the step is solved)
-      if ((r = refresh_at(j, F_REFRESH)) != SM_OK) return r;
       const Dev d_old = slot_dev(j > 0 ? j - 1 : 0), d_new = slot_dev(j);
       const int need = F_NEWTON | F_REFRESH;
-      for (int it = 0; it < kReplayIters; ++it) {
-        r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
-        if (r != SM_OK) return r;
-        if (j > 0) {
-          solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_old, need, F_NEWTON);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) {
+          rretry_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
           st->launches += 1;
         }
-        solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_new, need, need);
-        st->launches += 3;
+        if ((r = refresh_at(j, need)) != SM_OK) return r;
+        for (int it = 0; it < kReplayIters; ++it) {
+          r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
+          if (r != SM_OK) return r;
+          if (j > 0 && attempt == 0) {
+            solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_old, need, F_NEWTON);
+            st->launches += 1;
+          }
+          solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_new, need, need);
+          st->launches += 3;
+        }
       }
-      rcommit_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
+      rcommit_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, 1);
       st->launches += 1;
       if ((r = refresh_at(j, 0)) != SM_OK) return r;
     }
@@ -1700,12 +1789,82 @@ sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const 
   }
   SM_TRY_CUDA(cudaMemsetAsync(dd.counters + 2, 0, sizeof(int), s));
   adj_out_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, grad + c0, ldk, astat ? astat + c0 : nullptr);
+  st->launches += 1;
+  if (grad_y0) {
+    adj_y0_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, grad_y0 + c0, ldk);
+    st->launches += 1;
+  }
+  SM_TRY_CUDA(cudaGetLastError());
+  return adj_count_bad(st, bad);
+}
+
+// One pass of the frozen-step replay over cells [c0, c0 + Cp): the recorded
+// steps re-solved from the recorded initial state with rate coefficients k,
+// the Newton matrix refreshed by the gamma rule and every kCkpt steps, in the
+// state's own factor storage.
+sm_status replay_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const double* k, int64_t ldk,
+                      double* y, int32_t* astat, int64_t* bad) {
+  const sm_net* net = st->net;
+  cudaStream_t s = st->s;
+  Dev dd;
+  AdjDev a;
+  int Kmax = 0, Nmax = 0;
+  sm_status r = adj_prepare(st, c0, Cp, lda, k, ldk, nullptr, 0, &dd, &a, &Kmax, &Nmax);
+  if (r != SM_OK) return r;
+  const double* kp = k + c0;
+  double* scratch = st->scratch.as<double>() + c0;
+  const size_t solve_smem = sizeof(double) * (size_t)kSolveWarps * ((dd.n + 3) / 4 * 4);
+  seg_restore_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, -1);
+  st->launches += 1;
+  for (int j = 0; j < Nmax; ++j) {
+    rpredict_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, 0);
+    st->launches += 1;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (attempt == 1) {
+        rretry_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j);
+        st->launches += 1;
+      }
+      SM_TRY_CUDA(cudaMemsetAsync(dd.counters, 0, sizeof(int), s));
+      adj_list_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, F_NEWTON | F_REFRESH);
+      refresh_kernel<double><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(dd, kp, ldk, st->plan);
+      st->launches += 2;
+      for (int it = 0; it < kReplayIters; ++it) {
+        r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
+        if (r != SM_OK) return r;
+        solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(dd, F_NEWTON, F_NEWTON);
+        st->launches += 3;
+      }
+    }
+    rcommit_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, j, 0);
+    st->launches += 1;
+    SM_TRY_CUDA(cudaGetLastError());
+  }
+  SM_TRY_CUDA(cudaMemsetAsync(dd.counters + 2, 0, sizeof(int), s));
+  replay_out_kernel<<<blocks(Cp, 128), 128, 0, s>>>(dd, a, y + c0, ldk, astat ? astat + c0 : nullptr);
   SM_TRY_CUDA(cudaGetLastError());
   st->launches += 1;
-  SM_TRY_CUDA(cudaMemcpyAsync(st->h_counters, dd.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  SM_TRY_CUDA(cudaStreamSynchronize(s));
-  *bad += st->h_counters[2];
+  return adj_count_bad(st, bad);
+}
+
+// Workspace of the reverse sweep / replay for passes of Cc cells.
+sm_status adj_workspace(sm_state* st, int64_t Cc, int64_t lda, int n_cot) {
+  const int n = st->d.n, n_r = st->d.n_r;
+  const size_t nd = (size_t)kCkpt * n * lda + (size_t)kCkpt * lda + (size_t)kCkpt * (QMAX + 1) * lda +
+                    (size_t)kRing * (QMAX + 1) * lda + (size_t)kRing * n_cot * n * lda + (size_t)Cc * n_r +
+                    (size_t)Cc * n_cot * n_r;
+  const size_t ni = (size_t)(4 + kCkpt + kRing + 2) * lda;
+  sm_status r;
+  if ((r = st->adj_d.ensure(sizeof(double) * nd)) != SM_OK) return r;
+  if ((r = st->adj_i.ensure(sizeof(int) * ni)) != SM_OK) return r;
   return SM_OK;
+}
+
+// Cells per pass: all (0), or the request rounded up to a multiple of 32 so
+// that every pass starts on a 32-cell boundary.
+int64_t pass_cells(int64_t C, int64_t cells_per_pass) {
+  int64_t Cc = cells_per_pass > 0 ? std::min<int64_t>(cells_per_pass, C) : C;
+  if (Cc < C) Cc = std::min<int64_t>(C, (Cc + 31) / 32 * 32);
+  return Cc;
 }
 
 }  // namespace
@@ -1986,7 +2145,8 @@ sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, 
 }
 
 sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* d_cot, int32_t n_cot,
-                     double* d_grad, int32_t* d_astat, int64_t cells_per_pass, void* stream) {
+                     double* d_grad, double* d_grad_y0, int32_t* d_astat, int64_t cells_per_pass,
+                     void* stream) {
   if (!st || !d_k || !d_cot || !d_grad || n_cot < 1 || n_cot > SM_ADJ_MAX_COT || st->C < 1 ||
       !ld_ok(st->C, ld) || cells_per_pass < 0 || st->d.record < 1)
     return SM_EINVAL;
@@ -1996,15 +2156,9 @@ sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* 
   sm_status r;
   const int64_t C = st->C;
   const int n = st->d.n, n_r = st->d.n_r;
-  int64_t Cc = cells_per_pass > 0 ? std::min<int64_t>(cells_per_pass, C) : C;
-  if (Cc < C) Cc = std::min<int64_t>(C, (Cc + 31) / 32 * 32);  // passes start on 32-cell boundaries
+  const int64_t Cc = pass_cells(C, cells_per_pass);
   const int64_t lda = (Cc + 31) / 32 * 32;
-  const size_t nd = (size_t)kCkpt * n * lda + (size_t)kCkpt * lda + (size_t)kCkpt * (QMAX + 1) * lda +
-                    (size_t)kRing * (QMAX + 1) * lda + (size_t)kRing * n_cot * n * lda + (size_t)Cc * n_r +
-                    (size_t)Cc * n_cot * n_r;
-  const size_t ni = (size_t)(4 + kCkpt + kRing + 2) * lda;
-  if ((r = st->adj_d.ensure(sizeof(double) * nd)) != SM_OK) return r;
-  if ((r = st->adj_i.ensure(sizeof(int) * ni)) != SM_OK) return r;
+  if ((r = adj_workspace(st, Cc, lda, n_cot)) != SM_OK) return r;
   if ((r = st->adj_lu.ensure(sizeof(double) * (size_t)kCkpt * Cc * st->d.lu_stride)) != SM_OK) return r;
   const int warps = std::min(n_cot, 8);
   const size_t smem = sizeof(double) * ((size_t)n_r + (size_t)warps * 2 * n);
@@ -2016,7 +2170,29 @@ sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* 
   int64_t bad = 0;
   for (int64_t c0 = 0; c0 < C; c0 += Cc) {
     const int64_t Cp = std::min(Cc, C - c0);
-    r = adjoint_pass(st, c0, Cp, lda, d_k, ld, d_cot, n_cot, d_grad, d_astat, warps, smem, &bad);
+    r = adjoint_pass(st, c0, Cp, lda, d_k, ld, d_cot, n_cot, d_grad, d_grad_y0, d_astat, warps, smem, &bad);
+    if (r != SM_OK) return r;
+  }
+  if ((r = join_out(st, stream)) != SM_OK) return r;
+  return bad > 0 ? SM_EPARTIAL : SM_OK;
+}
+
+sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, int32_t* d_astat,
+                    int64_t cells_per_pass, void* stream) {
+  if (!st || !d_k || !d_y || st->C < 1 || !ld_ok(st->C, ld) || cells_per_pass < 0 || st->d.record < 1)
+    return SM_EINVAL;
+  if (st->d.mixed) return SM_ENOTSUP;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  const int64_t C = st->C;
+  const int64_t Cc = pass_cells(C, cells_per_pass);
+  const int64_t lda = (Cc + 31) / 32 * 32;
+  if ((r = adj_workspace(st, Cc, lda, 0)) != SM_OK) return r;
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  int64_t bad = 0;
+  for (int64_t c0 = 0; c0 < C; c0 += Cc) {
+    r = replay_pass(st, c0, std::min(Cc, C - c0), lda, d_k, ld, d_y, d_astat, &bad);
     if (r != SM_OK) return r;
   }
   if ((r = join_out(st, stream)) != SM_OK) return r;

@@ -115,11 +115,12 @@ def small(torch, B):
     yN = yd.cpu().numpy()[:, :C]
     cot, cot_d = log_cot(torch, d, yN, ld)
     grad = torch.zeros((N_COT, d.n_r, ld), dtype=torch.float64, device="cuda")
+    g0 = torch.zeros((N_COT, d.n_s, ld), dtype=torch.float64, device="cuda")
     astat = torch.full((ld,), -1, dtype=torch.int32, device="cuda")
-    code = st.adjoint(kd, cot_d, grad, astat)
+    code = st.adjoint(kd, cot_d, grad, astat, grad_y0=g0)
     torch.cuda.synchronize()
-    return dict(d=d, C=C, k=k, y0=y0, net=net, st=st, kd=kd, stats=stats, cot=cot, cot_d=cot_d,
-                grad=grad.cpu().numpy(), astat=astat.cpu().numpy()[:C], code=code)
+    return dict(d=d, C=C, k=k, y0=y0, net=net, st=st, kd=kd, yN=yN, stats=stats, cot=cot, cot_d=cot_d,
+                grad=grad.cpu().numpy(), grad_y0=g0.cpu().numpy(), astat=astat.cpu().numpy()[:C], code=code)
 
 
 def test_adjoint_matches_oracle_small(small):
@@ -129,8 +130,10 @@ def test_adjoint_matches_oracle_small(small):
     assert N.min() > 16          # every cell spans several checkpoint segments
     steps = recorded_steps(s["st"], N, s["C"])
     for c in (0, 1, 7, 19, 31, 32, 35):
-        ref = oracle_grad(s["d"], s["k"][:, c], s["y0"][:, c], steps[c], s["cot"][:, :, c])
+        ys = oa.frozen_forward(s["d"], s["k"][:, c], s["y0"][:, c], steps[c])
+        ref, ref0 = oa.adjoint(s["d"], s["k"][:, c], ys, steps[c], s["cot"][:, :, c], with_y0=True)
         check(s["grad"][:, :, c], ref, f"cell {c}")
+        check(s["grad_y0"][:, :, c], ref0, f"cell {c}, dPhi/dy0")
 
 
 def test_adjoint_pass_split_is_bit_identical(torch, B, small):
@@ -175,19 +178,19 @@ def test_adjoint_rejects_bad_calls(torch, B, small):
     grad = torch.zeros((N_COT, d.n_r, ld), dtype=torch.float64, device="cuda")
     p = lambda t: ct.c_void_p(t.data_ptr())
     # no cotangents, too many, negative pass size
-    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), 0, p(grad), None, 0, None) == B.SM_EINVAL
-    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), B.ADJ_MAX_COT + 1, p(grad), None, 0,
+    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), 0, p(grad), None, None, 0, None) == B.SM_EINVAL
+    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), B.ADJ_MAX_COT + 1, p(grad), None, None, 0,
                         None) == B.SM_EINVAL
-    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, -1, None) == B.SM_EINVAL
+    assert L.sm_adjoint(s["st"].h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, None, -1, None) == B.SM_EINVAL
     y0 = dev(torch, s["y0"], ld)
     # a state that records nothing
     st0 = B.State(s["net"], C)
     st0.init(s["kd"], y0, 1e3 * YEAR, C)
-    assert L.sm_adjoint(st0.h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, 0, None) == B.SM_EINVAL
+    assert L.sm_adjoint(st0.h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, None, 0, None) == B.SM_EINVAL
     # the adjoint runs in FP64 only
     stm = B.State(s["net"], C, precision="mixed", record_steps=100)
     stm.init(s["kd"], y0, 1e3 * YEAR, C)
-    assert L.sm_adjoint(stm.h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, 0, None) == B.SM_ENOTSUP
+    assert L.sm_adjoint(stm.h, p(s["kd"]), ld, p(s["cot_d"]), 1, p(grad), None, None, 0, None) == B.SM_ENOTSUP
     torch.cuda.synchronize()
 
 
@@ -215,3 +218,102 @@ def test_adjoint_matches_oracle_470x6000(torch, B):
     assert N[c] > 16
     ref = oracle_grad(d, k[:, c], y0[:, c], steps[c], cot[:, :, c])
     check(g[:, :, c], ref, f"cell {c}")
+
+
+def test_replay_matches_oracle_frozen_map(torch, B, small):
+    """sm_replay re-solves the recorded steps; the oracle's frozen map solves
+    the same steps to 1e-14.  The replay stops at 1e-4 in the run's WRMS
+    norm (rtol 1e-6), and the stable map carries that along the run, so the
+    bar is 1e-2 WRMS units (1e-8 relative) on every abundance."""
+    s = small
+    d, C = s["d"], s["C"]
+    ld = B.pad_ld(C)
+    y = torch.zeros((d.n_s, ld), dtype=torch.float64, device="cuda")
+    assert s["st"].replay(s["kd"], y) == B.SM_OK
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()[:, :C]
+    N = s["stats"]["steps"]
+    steps = recorded_steps(s["st"], N, C)
+    for c in (0, 5, 20, 33, 35):
+        ref = oa.frozen_forward(d, s["k"][:, c], s["y0"][:, c], steps[c])[-1]
+        w = 1e-6 * np.abs(ref) + 1e-20
+        assert np.max(np.abs(y[:, c] - ref) / w) <= 1e-2, c
+
+
+def test_autograd_function(torch, B, small):
+    """Integrate.apply + backward reproduces sm_adjoint with the same
+    cotangent: d/dlog k to one rounding (k.grad is divided by k), d/dy0 bit
+    for bit."""
+    from paper_2312_04998_gb300.autograd import Integrate
+    s = small
+    d, C = s["d"], s["C"]
+    ld = B.pad_ld(C)
+    st = B.State(s["net"], C, record_steps=4000, newton_tol=1e-3, newton_max=6)
+    k = s["kd"].clone().requires_grad_(True)
+    y0 = dev(torch, s["y0"], ld).requires_grad_(True)
+    y = Integrate.apply(k, y0, st, 1e3 * YEAR, C)
+    t = d.species_index("CO")
+    loss = torch.log(y[t, :C]).sum()
+    loss.backward()
+    # k.grad = (dPhi/dlog k) / k; multiplying back rounds once more
+    gk = (k.grad * k.detach()).cpu().numpy()[:, :C]
+    ref = s["grad"][0][:, :C]
+    assert np.all(np.abs(gk - ref) <= 4e-16 * np.abs(ref))
+    assert np.array_equal(y0.grad.cpu().numpy()[:, :C], s["grad_y0"][0][:, :C])
+    # a second integration invalidates the record of the first
+    y2 = Integrate.apply(k, y0, st, 1e3 * YEAR, C)
+    st.integrate(s["kd"], dev(torch, s["y0"], ld), 1e3 * YEAR, C)
+    with pytest.raises(RuntimeError):
+        torch.log(y2[t, :C]).sum().backward()
+
+
+def test_adjoint_central_differences_1024_cells(torch, B):
+    """The 1024-cell adjoint workload (470 x 6000, 1e5 yr, eight log-abundance
+    targets, checkpoints every 16 steps) against central differences of the
+    frozen map on the GPU: cell c perturbs one reaction j_c (half of them among
+    the largest gradient entries, half at random), so the two sm_replay calls
+    give 1024 sampled derivatives; 32 distinct reactions or more are covered.
+    Step h = 1e-4 in log k: the replay solves each step to 1e-10 relative, so
+    the difference quotient carries at most 1e-10 / h = 1e-6 of noise, while
+    the O(h^2) truncation stays near 1e-8 relative.  Bar: 1e-6 + 1e-4 |g|."""
+    from synth import workloads as W
+    desc, T, nH, Av, y0 = W.make("adjoint_470x6000_c1024")
+    C = y0.shape[1]
+    k = ok.rate_coefficients(desc, T, nH, Av)
+    ld = B.pad_ld(C)
+    net, st, kd, yd, stats, code = forward(torch, B, desc, k, y0, W.WORKLOADS["adjoint_470x6000_c1024"].t_end, 4000)
+    assert code == B.SM_OK
+    yr = torch.zeros_like(yd)
+    assert st.replay(kd, yr) == B.SM_OK
+    yN = yr.cpu().numpy()[:, :C]
+    frac = (yN > 1e-12).mean(axis=1)
+    targets = np.argsort(-frac, kind="stable")[:8]
+    cot = np.zeros((8, desc.n_s, ld))
+    for v, t in enumerate(targets):
+        cot[v, t, :C] = np.where(yN[t] > 1e-12, 1.0 / np.maximum(yN[t], 1e-300), 0.0)
+    grad = torch.zeros((8, desc.n_r, ld), dtype=torch.float64, device="cuda")
+    astat = torch.full((ld,), -1, dtype=torch.int32, device="cuda")
+    assert st.adjoint(kd, torch.tensor(cot, device="cuda"), grad, astat) == B.SM_OK
+    g = grad.cpu().numpy()[:, :, :C]
+    assert np.all(astat.cpu().numpy()[:C] == 0)
+    rng = np.random.default_rng(4998)
+    vs = np.arange(C) % 8
+    js = np.array([int(np.argsort(-np.abs(g[vs[c], :, c]))[rng.integers(0, 8)]) if c % 2 == 0
+                   else int(rng.integers(0, desc.n_r)) for c in range(C)])
+    assert len(set(js.tolist())) >= 32
+    hh = 1e-4
+    out = []
+    for sign in (1.0, -1.0):
+        kp = k.copy()
+        kp[js, np.arange(C)] *= np.exp(sign * hh)
+        y = torch.zeros_like(yd)
+        assert st.replay(dev(torch, kp, ld), y) == B.SM_OK
+        out.append(y.cpu().numpy()[:, :C])
+    live = cot[vs, targets[vs], np.arange(C)] != 0
+    phi = [np.log(np.where(live, Y[targets[vs], np.arange(C)], 1.0)) for Y in out]
+    fd = (phi[0] - phi[1]) / (2 * hh)
+    ad = g[vs, js, np.arange(C)]
+    err = np.abs(fd - ad)[live]
+    bar = 1e-6 + 1e-4 * np.abs(ad[live])
+    assert live.sum() >= 0.9 * C
+    assert np.all(err <= bar), float((err / bar).max())
