@@ -39,7 +39,7 @@ TRAFFIC = {}
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -50,6 +50,10 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-cells", type=int, default=0, help="oracle sample size (0 = host cores)")
+    p.add_argument("--fp64-cells", type=int, default=4096,
+                   help="cells of the plain FP64 comparison integrate (0 = skip)")
+    p.add_argument("--adjoint-cells", type=int, default=1024,
+                   help="cells of the adjoint/forward measurement (0 = skip)")
     return p.parse_args()
 
 
@@ -172,6 +176,104 @@ def clocks_stop(proc):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def timed(fn, stream):
+    """Runs fn() between CUDA events on `stream`; returns (result, ms)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1)
+
+
+def gpu_inputs(B, net, d, T, nH, Av, y0, dev):
+    """Device k' (evaluated by sm_rates_eval) and y0 for C cells."""
+    import torch
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+
+    def padded(v, fill):
+        out = torch.full((ld,), fill, dtype=torch.float64, device=dev)
+        out[:C] = torch.tensor(v, dtype=torch.float64, device=dev)
+        return out
+
+    kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
+    net.rates_eval(padded(T, 100.0), padded(nH, 1.0), padded(Av, 0.0), kd, C)
+    y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
+    y0d[:, :C] = torch.tensor(y0, dtype=torch.float64, device=dev)
+    return kd, y0d
+
+
+def fp64_comparison(B, net, d, T, nH, Av, y0, t_end, dev):
+    """The plain FP64 integrator on the first cells of the same workload
+    (FP64-pipe bound at any batch that fills the GPU, so its cell-steps/s is
+    that of the full batch); one short untimed warm-up."""
+    import torch
+    C = y0.shape[1]
+    st = B.State(net, C, precision="fp64")
+    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
+    stats = B.stats_tensor(C, dev)
+    yd = y0d.clone()
+    st.integrate(kd, yd, 1e-3 * t_end, C, stats)
+    stream = torch.cuda.current_stream(dev)
+    yd.copy_(y0d)
+    _, ms = timed(lambda: st.integrate(kd, yd, t_end, C, stats), stream)
+    s = B.stats_to_numpy(stats)
+    launches, _, _ = st.timing()
+    st.close()
+    return {"cells": C, "value": float(s["steps"].sum()) / (ms * 1e-3), "unit": UNIT, "ms": ms,
+            "steps_per_cell": float(s["steps"].mean()), "cells_ok": int((s["status"] == 0).sum())}
+
+
+def adjoint_measurement(B, C, dev):
+    """Discrete adjoint on the adjoint workload (470 x 6000, 1e5 yr, FP64,
+    checkpoints every 16 steps): one recorded forward integrate and one reverse
+    sweep for eight log-abundance targets, each timed with CUDA events.
+    Targets: the eight species above 1e-12 in the largest share of cells at
+    t_end (cotangent 1/y there, 0 in cells where the species is below)."""
+    import numpy as np
+    import torch
+    from synth.workloads import WORKLOADS, make
+    name = "adjoint_470x6000_c1024"
+    d, T, nH, Av, y0 = make(name, cells=C)
+    t_end = WORKLOADS[name].t_end
+    net = B.Network(d, dev.index or 0)
+    st = B.State(net, C, precision="fp64", record_steps=8000)
+    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
+    stats = B.stats_tensor(C, dev)
+    yd = y0d.clone()
+    stream = torch.cuda.current_stream(dev)
+    st.integrate(kd, yd, 1e-3 * t_end, C, stats)      # warm-up (graph capture)
+    yd.copy_(y0d)
+    code_f, f_ms = timed(lambda: st.integrate(kd, yd, t_end, C, stats), stream)
+    s = B.stats_to_numpy(stats)
+    yN = yd.cpu().numpy()[:, :C]
+    ld = B.pad_ld(C)
+    frac = (yN > 1e-12).mean(axis=1)
+    targets = np.argsort(-frac, kind="stable")[:8]
+    cot = np.zeros((8, d.n_s, ld))
+    for v, t in enumerate(targets):
+        cot[v, t, :C] = np.where(yN[t] > 1e-12, 1.0 / np.maximum(yN[t], 1e-300), 0.0)
+    cot_d = torch.tensor(cot, dtype=torch.float64, device=dev)
+    grad = torch.zeros((8, d.n_r, ld), dtype=torch.float64, device=dev)
+    astat = torch.zeros(ld, dtype=torch.int32, device=dev)
+    l0, _, _ = st.timing()
+    code_a, a_ms = timed(lambda: st.adjoint(kd, cot_d, grad, astat), stream)
+    l1, _, _ = st.timing()
+    out = {"workload": name, "cells": C, "t_end_yr": t_end / YEAR, "n_cot": 8,
+           "targets": [d.names[t] for t in targets], "forward_ms": f_ms, "adjoint_ms": a_ms,
+           "adjoint_per_forward": a_ms / f_ms, "adjoint_ms_per_target": a_ms / 8,
+           "steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
+           "cells_ok": int((astat.cpu().numpy()[:C] == 0).sum()), "forward_status": int(code_f),
+           "adjoint_status": int(code_a), "adjoint_launches": int(l1 - l0),
+           "checkpoint_every": B.CHECKPOINT_EVERY}
+    st.close()
+    net.close()
+    return out
+
 
 def kernel_source_hash():
     h = hashlib.sha256()
@@ -332,6 +434,12 @@ def main():
                 "kernel": f"{a.time_kernel} ({'FP32' if fp32 else 'FP64'} pipe)",
                 "avg_launch_ms": kern_ms / kern_n, "timed_launches": kern_n,
                 "peak_source": "unit counts x 2.07 GHz max SM clock: FP32 152x128x2, FP64 152x4 flops/clk"}
+    fp64 = None
+    if a.fp64_cells > 0 and a.precision == "mixed":
+        n = min(a.fp64_cells, C)
+        fp64 = fp64_comparison(B, net, d, T[:n], nH[:n], Av[:n], np.ascontiguousarray(y0[:, :n]), t_end, dev)
+    del state
+    adj = adjoint_measurement(B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     cpu = None
     if not a.no_cpu:
         n = a.cpu_cells or host_cores()
@@ -354,6 +462,7 @@ def main():
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "fp64": fp64, "adjoint": adj,
     }
     print(json.dumps(out))
 

@@ -106,6 +106,7 @@ _SIGS = [
                                ct.c_int64, ct.c_void_p]),
 ]
 ADJ_MAX_COT = 64
+CHECKPOINT_EVERY = 16
 
 
 def lib():

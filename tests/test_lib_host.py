@@ -35,6 +35,14 @@ def test_library_exports_every_declared_symbol(B):
         assert hasattr(L, name), name
 
 
+def test_binding_constants_match_header(B):
+    src = open(os.path.join(ROOT, "include", "stoich.h")).read()
+    defs = dict(re.findall(r"#define\s+(SM_[A-Z_]+)\s+(\d+)", src))
+    assert int(defs["SM_CHECKPOINT_EVERY"]) == B.CHECKPOINT_EVERY
+    assert int(defs["SM_ADJ_MAX_COT"]) == B.ADJ_MAX_COT
+    assert int(defs["SM_STATIC_SCRATCH_DOUBLES"]) == B.STATIC_SCRATCH_DOUBLES
+
+
 def test_status_strings(B):
     assert B.status_str(B.SM_OK) == "ok"
     assert "conserve" in B.status_str(B.SM_ENOTCONS)
