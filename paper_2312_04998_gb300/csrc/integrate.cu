@@ -1414,6 +1414,7 @@ struct sm_state {
   cudaGraphExec_t graph = nullptr;
   const double* graph_k = nullptr;
   int64_t graph_ldk = 0, graph_C = 0;
+  double graph_t_end = 0.0;   // the captured kernels hold Dev by value, t_end included
   int refresh_ctas = 0;
   RefreshPlan plan{};
   // instrumentation
@@ -1572,7 +1573,7 @@ sm_status enqueue_group(sm_state* st, const double* k, int64_t ldk, int attempts
 }
 
 // Runs `attempts` attempts on the state's stream, through a cached CUDA graph
-// when enabled (captured once per (k, ldk, C)).
+// when enabled (captured once per (k, ldk, C, t_end)).
 sm_status run_attempts(sm_state* st, const double* k, int64_t ldk, int attempts) {
   if (!st->opts.use_graph) {
     sm_status r = enqueue_group(st, k, ldk, attempts, st->s);
@@ -1583,7 +1584,8 @@ sm_status run_attempts(sm_state* st, const double* k, int64_t ldk, int attempts)
     return r;
   }
   const int per = st->opts.attempts_per_sync;
-  if (!st->graph || st->graph_k != k || st->graph_ldk != ldk || st->graph_C != st->d.C) {
+  if (!st->graph || st->graph_k != k || st->graph_ldk != ldk || st->graph_C != st->d.C ||
+      st->graph_t_end != st->d.t_end) {
     if (st->graph) {
       cudaGraphExecDestroy(st->graph);
       st->graph = nullptr;
@@ -1607,6 +1609,7 @@ sm_status run_attempts(sm_state* st, const double* k, int64_t ldk, int attempts)
     st->graph_k = k;
     st->graph_ldk = ldk;
     st->graph_C = st->d.C;
+    st->graph_t_end = st->d.t_end;
   }
   for (int done = 0; done < attempts; done += per) {
     if (attempts - done >= per) {

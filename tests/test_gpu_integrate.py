@@ -186,3 +186,29 @@ def test_large_network_matches_oracle(torch, B, precision):
     assert e_g <= factor * max(e_o, 1.0), (e_g, e_o)
     E = on.element_matrix(d).astype(float)
     assert np.allclose(E[:3] @ y, E[:3] @ y0, rtol=1e-12)
+
+
+def test_state_reuse_with_new_end_time(torch, B):
+    """A state integrated once to a short end time and then to a long one
+    gives the same bits as a fresh state integrated to the long one (the
+    cached graph of attempts must not keep the first end time)."""
+    d = sn.generate(2312, 32, 180)
+    C = 40
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
+    k = ok.rate_coefficients(d, T, nH, Av)
+    y0 = sc.atomic_start(d, C)
+    ld = B.pad_ld(C)
+    net = B.Network(d, 0)
+    kd = dev(torch, k, ld)
+    out = []
+    for ends in ((1e2 * YEAR, 1e5 * YEAR), (1e5 * YEAR,)):
+        st = B.State(net, C)
+        for t_end in ends:
+            yd = dev(torch, y0, ld)
+            stats = B.stats_tensor(C, "cuda")
+            assert st.integrate(kd, yd, t_end, C, stats) == B.SM_OK
+        torch.cuda.synchronize()
+        s = B.stats_to_numpy(stats)
+        assert np.all(s["t"] == 1e5 * YEAR)
+        out.append((yd.cpu().numpy(), s["steps"].copy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
