@@ -81,6 +81,7 @@ void release_all(sm_net* net) {
   lu.d_lrhoff.release();
   lu.d_u12off.release();
   lu.d_lrhk.release();
+  lu.d_srow.release();
   net->d_jt_slot.release();
   net->d_sc_ptr.release();
   net->d_sc_ent.release();

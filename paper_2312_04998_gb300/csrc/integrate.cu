@@ -54,8 +54,8 @@ struct Dev {
   int64_t lu_stride;
   int ldm;
   const int *perm, *iperm, *lptr, *lidx, *uptr, *uidx, *lrptr, *lridx, *ucptr, *ucidx, *jp_ptr, *jt_ptr,
-      *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk;
-  void* l21_scratch;
+      *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk, *srow;
+  int n_srow;
   const int2 *jt_word, *jt_slot, *reac;
   const int* sc_ptr;
   const uint32_t* sc_ent;
@@ -243,11 +243,12 @@ __global__ void predict_kernel(Dev d) {
 //  B  A11 is factorised in shared memory by one warp; the rows of
 //     L21 = A21 U11^-1 and the columns of U12 = L11^-1 A12 are solved one
 //     warp each (entries held by lanes, resolved in order with shuffles);
+//  S  the head's Schur complement A22 -= L21 U12 (sparse: about 1 % of a
+//     dense product) is applied panel by panel from shared memory: U12's
+//     panel columns as a dense tile, L21 in compact row order, one warp per
+//     tail row (lanes = columns), rows dealt longest first;
 //  C  the trailing block is factorised right-looking by panels of kNB
-//     columns.  The head's Schur complement -L21 U12 is not applied up front:
-//     each trailing entry receives it when it is loaded into its panel or U
-//     block, the one time it is read before it is final (the additions
-//     commute).  Panel and U12 block live in shared memory; the trailing
+//     columns; panel and U12 block live in shared memory, the trailing
 //     update is a register-tiled GEMM.
 // Inverse pivots replace the diagonal.
 // ---------------------------------------------------------------------------
@@ -266,6 +267,7 @@ struct RefreshPlan {
   int upitch;         // row pitch of the U block buffer
   int n_u12;          // staged U12 entries (head rows, tail columns)
   int n_l21;          // L21 entries (tail rows, head columns)
+  int l21_off;        // byte offset of the compact L21 (values, then u16 head columns) in phase B/S
   int n_panels;       // 32-wide panels of the trailing block
   bool head_smem;     // phase B with A11 in shared memory (else pivot by pivot)
   size_t bytes;
@@ -311,8 +313,9 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
   double* coef = dR + 2 * n_r;                      // (double)(int8_t)i, J coefficients
   wsf = reinterpret_cast<float*>(coef + 256);
   wif = wsf + n;
-  // this CTA's copy of L21 in compact row order (phase B writes, phase C reads)
-  T* l21 = static_cast<T*>(d.l21_scratch) + (size_t)blockIdx.x * plan.n_l21;
+  // compact L21 (tail rows' head entries, row order): phase B writes, phase S reads
+  T* l21s = reinterpret_cast<T*>(smem_raw + plan.l21_off);
+  unsigned short* l21k = reinterpret_cast<unsigned short*>(l21s + plan.n_l21);
   const int count = d.counters[0];
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t c = d.list[e];
@@ -450,7 +453,8 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         for (int g = 0; g < kHeadG; ++g)
           if (lane + 32 * g < cnt) {
             Ai[kc[g]] = av[g];
-            l21[o + lane + 32 * g] = av[g];
+            l21s[o + lane + 32 * g] = av[g];
+            l21k[o + lane + 32 * g] = (unsigned short)kc[g];
           }
       }
       // U12 columns (warp per column): u_kj = a_kj - sum_{m<k} l_km u_mj
@@ -502,6 +506,37 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         for (int b = lane; b < np1; b += 32) su_off[kr * np1 + b] = o + __ldg(d.uoff + kr * np1 + b) - q0;
       }
       __syncthreads();
+      // ---- phase S: A22 -= L21 U12, one 32-column panel at a time.  U12's
+      // panel columns are expanded into a dense h x 32 tile (over A11, no
+      // longer needed); each tail row with head entries is one warp's: lanes
+      // are the panel's columns, the row's (l, k) pairs come from shared memory.
+      T* Ut = reinterpret_cast<T*>(smem_raw);
+      for (int q = 0; q < plan.n_panels; ++q) {
+        const int c0 = h + kNB * q, wq = min(kNB, n - c0);
+        for (int e = tid; e < h * kNB; e += nthr) Ut[e] = T(0);
+        __syncthreads();
+        for (int kr = warp; kr < h; kr += nwarps) {
+          const int e1 = su_off[kr * np1 + q + 1];
+          for (int e = su_off[kr * np1 + q] + lane; e < e1; e += 32)
+            Ut[kr * kNB + ((int)su_col[e] - kNB * q)] = su_val[e];
+        }
+        __syncthreads();
+        for (int t = warp; t < d.n_srow; t += nwarps) {
+          const int ir = __ldg(d.srow + t);
+          const int o = __ldg(d.lrhoff + ir), cnt = __ldg(d.lrhead + ir);
+          T* Ai = A + (int64_t)(h + ir) * ldm + c0;
+          const T cur = lane < wq ? Ai[lane] : T(0);
+          T a0 = T(0), a1 = T(0);
+          int u = 0;
+          for (; u + 1 < cnt; u += 2) {
+            a0 += l21s[o + u] * Ut[(int)l21k[o + u] * kNB + lane];
+            a1 += l21s[o + u + 1] * Ut[(int)l21k[o + u + 1] * kNB + lane];
+          }
+          if (u < cnt) a0 += l21s[o + u] * Ut[(int)l21k[o + u] * kNB + lane];
+          if (lane < wq) Ai[lane] = cur - (a0 + a1);
+        }
+        __syncthreads();
+      }
     } else {
       // pivot by pivot, Schur complement applied immediately
       for (int kp = 0; kp < h; ++kp) {
@@ -533,33 +568,6 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       for (int a = m + tid; a < pitch; a += nthr)
         for (int b = 0; b < w; ++b) Pt[b * pitch + a] = T(0);
       __syncthreads();
-      if (plan.head_smem && h > 0) {
-        // pending head contributions -sum_k l_ik u_kj to the panel; each
-        // thread owns rows, its (k, l) pairs come in batches of 8 independent
-        // loads from the compact L21 copy
-        for (int a = tid; a < m; a += nthr) {
-          const int i = p0 + a;
-          const int o = __ldg(d.lrhoff + i - h), cnt = __ldg(d.lrhead + i - h);
-          for (int q0 = 0; q0 < cnt; q0 += 8) {
-            int kb[8];
-            T lb[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const bool ok = q0 + u < cnt;
-              kb[u] = ok ? (__ldg(d.lrhk + o + q0 + u)) : 0;
-              lb[u] = ok ? l21[o + q0 + u] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              if (q0 + u >= cnt) break;
-              const int e1 = su_off[kb[u] * np1 + pb + 1];
-              for (int e = su_off[kb[u] * np1 + pb]; e < e1; ++e)
-                Pt[((int)su_col[e] + h - p0) * pitch + a] -= lb[u] * su_val[e];
-            }
-          }
-        }
-        __syncthreads();
-      }
       for (int kk = 0; kk < w; ++kk) {
         // row kk is final after the previous barrier; the inverse pivot is
         // stored after this step's barrier (no later step reads it)
@@ -581,22 +589,6 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
           for (int b = lane; b < rp; b += 32)
             U[a * upitch + b] = b < r ? A[(int64_t)(p0 + a) * ldm + p0 + w + b] : T(0);
         __syncthreads();
-        if (plan.head_smem && h > 0) {
-          // pending head contributions to the rows of the U block (warp per row)
-          for (int a = warp; a < w; a += nwarps) {
-            const int i = p0 + a;
-            const int o = __ldg(d.lrhoff + i - h), cnt = __ldg(d.lrhead + i - h);
-            for (int q = 0; q < cnt; ++q) {
-              const int kc = __ldg(d.lrhk + o + q);
-              const T l = l21[o + q];
-              const int e1 = su_off[kc * np1 + plan.n_panels];
-              for (int e = su_off[kc * np1 + pb + 1] + lane; e < e1; e += 32)
-                U[a * upitch + ((int)su_col[e] + h - p0 - w)] -= l * su_val[e];
-              __syncwarp();
-            }
-          }
-          __syncthreads();
-        }
         // U12 = L11^-1 A12, one thread per column
         if (w == kNB) {
           for (int b = tid; b < r; b += nthr) {
@@ -1406,7 +1398,7 @@ struct sm_state {
   int64_t cap = 0, C = 0, ld = 0;
   double t_end = 0.0;
   Dev d{};
-  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, l21, rec_d, rec_i;
+  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, rec_d, rec_i;
   DevArray adj_d, adj_i, adj_lu;   // sm_adjoint workspace, grown on demand
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1478,7 +1470,6 @@ void free_state(sm_state* st) {
   st->list.release();
   st->counters.release();
   st->scratch.release();
-  st->l21.release();
   st->rec_d.release();
   st->rec_i.release();
   st->adj_d.release();
@@ -1955,6 +1946,8 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.lrhoff = lu.d_lrhoff.as<int>();
   d.u12off = lu.d_u12off.as<int>();
   d.lrhk = lu.d_lrhk.as<int>();
+  d.srow = lu.d_srow.as<int>();
+  d.n_srow = (int)lu.srow.size();
   d.jt_slot = net->d_jt_slot.as<int2>(); d.reac = net->d_reac.as<int2>();
   d.sc_ptr = net->d_sc_ptr.as<int>(); d.sc_ent = net->d_sc_ent.as<uint32_t>();
   d.jp_ptr = net->d_jp_ptr.as<int>(); d.jt_ptr = net->d_jt_ptr.as<int>();
@@ -2004,10 +1997,15 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
       max_l21 = std::max(max_l21, cnt);
     }
     for (int j = 0; j + 1 < (int)lu.ucptr.size(); ++j) max_u12 = std::max(max_u12, lu.ucptr[j + 1] - lu.ucptr[j]);
-    // A11 must not overlap the staged U12 (written while A11 is still read)
-    const size_t head_b = esz * (size_t)kNB * (pl.pitch + pl.upitch) + stage_u12;
-    pl.head_smem = lu.head > 0 && a11 <= esz * (size_t)kNB * (pl.pitch + pl.upitch) &&
-                   head_b <= (size_t)smem_max && max_l21 <= kHeadLanes && max_u12 <= kHeadLanes;
+    // phases B and S: A11 (then the U12 panel tile), the compact L21 and the
+    // staged U12 must not overlap (U12 is staged while A11 is still read)
+    const size_t su_start = esz * (size_t)kNB * (pl.pitch + pl.upitch);
+    const size_t l21_off = ((std::max(a11, esz * (size_t)lu.head * kNB) + 15) / 16) * 16;
+    const size_t l21_end = l21_off + (esz + 2) * (size_t)pl.n_l21;
+    pl.l21_off = (int)l21_off;
+    const size_t head_b = su_start + stage_u12;
+    pl.head_smem = lu.head > 0 && l21_end <= su_start && head_b <= (size_t)smem_max &&
+                   max_l21 <= kHeadLanes && max_u12 <= kHeadLanes;
     pl.bytes = std::max(tail, stage);
     if (pl.head_smem) pl.bytes = std::max(pl.bytes, a11);
   }
@@ -2029,10 +2027,6 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<double>, kRefreshThreads, rsm);
   }
   st->refresh_ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  // compact L21 copies, one per refresh CTA (the grid is exactly refresh_ctas)
-  if ((r = st->l21.ensure(esz * (size_t)std::max(st->plan.n_l21, 1) * (size_t)st->refresh_ctas)) != SM_OK)
-    return fail(r);
-  d.l21_scratch = st->l21.p;
   SM_TRY_CUDA(cudaMemset(st->scal_i.p, 0, st->scal_i.bytes));
   *out = st;
   return SM_OK;
@@ -2049,7 +2043,7 @@ sm_status sm_state_free(sm_state* st) {
 sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
   if (!st || !bytes) return SM_EINVAL;
   *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->list.bytes +
-           st->counters.bytes + st->scratch.bytes + st->l21.bytes + st->rec_d.bytes + st->rec_i.bytes + st->adj_d.bytes + st->adj_i.bytes +
+           st->counters.bytes + st->scratch.bytes + st->rec_d.bytes + st->rec_i.bytes + st->adj_d.bytes + st->adj_i.bytes +
            st->adj_lu.bytes;
   return SM_OK;
 }

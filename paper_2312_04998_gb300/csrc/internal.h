@@ -73,12 +73,13 @@ struct LUSymbolic {
   std::vector<int32_t> lrhoff;            // exclusive prefix sum of lrhead (n - head + 1 entries)
   std::vector<int32_t> u12off;            // per head row: start of its tail-column U entries, packed
   std::vector<int32_t> lrhk;              // head column of each L21 entry in compact row order
+  std::vector<int32_t> srow;              // tail rows with L21 entries, longest first
   std::vector<int32_t> uoff;              // per head row k: [n_panels + 1] offsets into its U list where
                                           // the tail columns of each 32-wide panel start
   std::vector<int32_t> jpos;              // per J pattern entry: dense offset p*ld+q
   int64_t nnz = 0, flops = 0;
   DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_ucptr, d_ucidx, d_jpos, d_perm, d_iperm,
-      d_jrc, d_uoff, d_lrhead, d_lrhoff, d_u12off, d_lrhk;
+      d_jrc, d_uoff, d_lrhead, d_lrhoff, d_u12off, d_lrhk, d_srow;
 };
 
 struct sm_net {

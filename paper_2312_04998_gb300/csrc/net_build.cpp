@@ -313,6 +313,13 @@ void build_lu_symbolic(sm_net& net) {
   lu.lrhk.clear();
   for (int32_t i = lu.head; i < n; ++i)
     for (int32_t q = 0; q < lu.lrhead[i - lu.head]; ++q) lu.lrhk.push_back(lu.lridx[lu.lrptr[i] + q]);
+  // tail rows that receive head contributions, longest L21 row first (the
+  // refresh kernel deals them to warps round-robin)
+  lu.srow.clear();
+  for (int32_t i = 0; i < n - lu.head; ++i)
+    if (lu.lrhead[i] > 0) lu.srow.push_back(i);
+  std::stable_sort(lu.srow.begin(), lu.srow.end(),
+                   [&](int32_t a, int32_t b) { return lu.lrhead[a] > lu.lrhead[b]; });
   {
     const int32_t np1 = (n - lu.head + 31) / 32 + 1;
     lu.u12off.assign(1, 0);
@@ -653,6 +660,7 @@ sm_status net_upload(sm_net* net) {
   if ((st = lu.d_lrhoff.upload(lu.lrhoff.data(), lu.lrhoff.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_u12off.upload(lu.u12off.data(), lu.u12off.size() * 4)) != SM_OK) return st;
   if (!lu.lrhk.empty() && (st = lu.d_lrhk.upload(lu.lrhk.data(), lu.lrhk.size() * 4)) != SM_OK) return st;
+  if (!lu.srow.empty() && (st = lu.d_srow.upload(lu.srow.data(), lu.srow.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_perm.upload(lu.perm.data(), lu.perm.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_iperm.upload(lu.iperm.data(), lu.iperm.size() * 4)) != SM_OK) return st;
   int32_t zero = 0;
