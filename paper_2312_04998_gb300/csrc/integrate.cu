@@ -521,19 +521,37 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
             Ut[kr * kNB + ((int)su_col[e] - kNB * q)] = su_val[e];
         }
         __syncthreads();
-        for (int t = warp; t < d.n_srow; t += nwarps) {
-          const int ir = __ldg(d.srow + t);
-          const int o = __ldg(d.lrhoff + ir), cnt = __ldg(d.lrhead + ir);
-          T* Ai = A + (int64_t)(h + ir) * ldm + c0;
-          const T cur = lane < wq ? Ai[lane] : T(0);
-          T a0 = T(0), a1 = T(0);
-          int u = 0;
-          for (; u + 1 < cnt; u += 2) {
-            a0 += l21s[o + u] * Ut[(int)l21k[o + u] * kNB + lane];
-            a1 += l21s[o + u + 1] * Ut[(int)l21k[o + u + 1] * kNB + lane];
+        // kSB rows per warp at a time (rows t = t0 + u * nwarps + warp, so the
+        // longest rows stay spread over the warps): their loads of A go out
+        // together before any row's sum is formed
+        constexpr int kSB = 8;
+        for (int t0 = 0; t0 < d.n_srow; t0 += kSB * nwarps) {
+          T cur[kSB];
+          int ir[kSB], ro[kSB], rc[kSB];
+#pragma unroll
+          for (int u = 0; u < kSB; ++u) {
+            const int t = t0 + u * nwarps + warp;
+            ir[u] = t < d.n_srow ? __ldg(d.srow + t) : -1;
           }
-          if (u < cnt) a0 += l21s[o + u] * Ut[(int)l21k[o + u] * kNB + lane];
-          if (lane < wq) Ai[lane] = cur - (a0 + a1);
+#pragma unroll
+          for (int u = 0; u < kSB; ++u) {
+            cur[u] = (ir[u] >= 0 && lane < wq) ? A[(int64_t)(h + ir[u]) * ldm + c0 + lane] : T(0);
+            ro[u] = ir[u] >= 0 ? __ldg(d.lrhoff + ir[u]) : 0;
+            rc[u] = ir[u] >= 0 ? __ldg(d.lrhead + ir[u]) : 0;
+          }
+#pragma unroll
+          for (int u = 0; u < kSB; ++u) {
+            if (ir[u] < 0) continue;
+            const int o = ro[u], cnt = rc[u];
+            T a0 = T(0), a1 = T(0);
+            int e = 0;
+            for (; e + 1 < cnt; e += 2) {
+              a0 += l21s[o + e] * Ut[(int)l21k[o + e] * kNB + lane];
+              a1 += l21s[o + e + 1] * Ut[(int)l21k[o + e + 1] * kNB + lane];
+            }
+            if (e < cnt) a0 += l21s[o + e] * Ut[(int)l21k[o + e] * kNB + lane];
+            if (lane < wq) A[(int64_t)(h + ir[u]) * ldm + c0 + lane] = cur[u] - (a0 + a1);
+          }
         }
         __syncthreads();
       }
@@ -568,19 +586,63 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       for (int a = m + tid; a < pitch; a += nthr)
         for (int b = 0; b < w; ++b) Pt[b * pitch + a] = T(0);
       __syncthreads();
-      for (int kk = 0; kk < w; ++kk) {
-        // row kk is final after the previous barrier; the inverse pivot is
-        // stored after this step's barrier (no later step reads it)
-        const T inv = T(1) / Pt[kk * pitch + kk];
-        for (int a = kk + 1 + tid; a < m; a += nthr) {
-          const T l = Pt[kk * pitch + a] * inv;
-          Pt[kk * pitch + a] = l;
-          for (int b = kk + 1; b < w; ++b) Pt[b * pitch + a] -= l * Pt[b * pitch + kk];
+      if (sizeof(T) == 4 && w == kNB) {
+        // full FP32 panel.  (1) warp 0 factors the kNB x kNB diagonal block in
+        // registers (lane = row, pivot rows broadcast by shuffles); (2) every
+        // row below solves l U11 = a on its own (thread per row, U11 read as
+        // shared-memory broadcasts), with no barrier between columns
+        if (warp == 0) {
+          T rv[kNB];
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) rv[b] = Pt[b * pitch + lane];
+#pragma unroll
+          for (int kk = 0; kk < kNB; ++kk) {
+            const T inv = T(1) / shfl(rv[kk], kk);
+            const T l = rv[kk] * inv;
+            const bool below = lane > kk;
+            if (below) rv[kk] = l;
+#pragma unroll
+            for (int b = 0; b < kNB; ++b)
+              if (b > kk) {
+                const T pb = shfl(rv[b], kk);
+                if (below) rv[b] -= l * pb;
+              }
+          }
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) Pt[b * pitch + lane] = b == lane ? T(1) / rv[b] : rv[b];
         }
         __syncthreads();
-        if (tid == 0) Pt[kk * pitch + kk] = inv;
+        for (int a = kNB + tid; a < m; a += nthr) {
+          T rv[kNB];
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) rv[b] = Pt[b * pitch + a];
+#pragma unroll
+          for (int kk = 0; kk < kNB; ++kk) {
+            const T l = rv[kk] * Pt[kk * pitch + kk];   // inverse pivot
+            rv[kk] = l;
+#pragma unroll
+            for (int b = 0; b < kNB; ++b)
+              if (b > kk) rv[b] -= l * Pt[b * pitch + kk];
+          }
+#pragma unroll
+          for (int b = 0; b < kNB; ++b) Pt[b * pitch + a] = rv[b];
+        }
+        __syncthreads();
+      } else {
+        for (int kk = 0; kk < w; ++kk) {
+          // row kk is final after the previous barrier; the inverse pivot is
+          // stored after this step's barrier (no later step reads it)
+          const T inv = T(1) / Pt[kk * pitch + kk];
+          for (int a = kk + 1 + tid; a < m; a += nthr) {
+            const T l = Pt[kk * pitch + a] * inv;
+            Pt[kk * pitch + a] = l;
+            for (int b = kk + 1; b < w; ++b) Pt[b * pitch + a] -= l * Pt[b * pitch + kk];
+          }
+          __syncthreads();
+          if (tid == 0) Pt[kk * pitch + kk] = inv;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       for (int a = warp; a < m; a += nwarps)
         if (lane < w) A[(int64_t)(p0 + a) * ldm + p0 + lane] = Pt[lane * pitch + a];
       if (r > 0) {
