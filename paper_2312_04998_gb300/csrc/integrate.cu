@@ -258,6 +258,7 @@ constexpr int kTM = 4, kTN = 4;
 constexpr int kBM = 16 * kTM, kBN = 16 * kTN;
 constexpr int kHeadG = 4;                 // head entries held per lane
 constexpr int kHeadLanes = 32 * kHeadG;   // longest L21 row / U12 column held in a warp
+constexpr int kPS = 3;                    // panels per pass of the head Schur complement (phase S)
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -511,22 +512,25 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       // longer needed); each tail row with head entries is one warp's: lanes
       // are the panel's columns, the row's (l, k) pairs come from shared memory.
       T* Ut = reinterpret_cast<T*>(smem_raw);
-      for (int q = 0; q < plan.n_panels; ++q) {
-        const int c0 = h + kNB * q, wq = min(kNB, n - c0);
-        for (int e = tid; e < h * kNB; e += nthr) Ut[e] = T(0);
+      for (int q0 = 0; q0 < plan.n_panels; q0 += kPS) {
+        // kPS panels per pass: tile [j][k][32] for panel q0 + j
+        const int np = min(kPS, plan.n_panels - q0);
+        for (int e = tid; e < np * h * kNB; e += nthr) Ut[e] = T(0);
         __syncthreads();
         for (int kr = warp; kr < h; kr += nwarps) {
-          const int e1 = su_off[kr * np1 + q + 1];
-          for (int e = su_off[kr * np1 + q] + lane; e < e1; e += 32)
-            Ut[kr * kNB + ((int)su_col[e] - kNB * q)] = su_val[e];
+          const int e1 = su_off[kr * np1 + q0 + np];
+          for (int e = su_off[kr * np1 + q0] + lane; e < e1; e += 32) {
+            const int ct = (int)su_col[e] - kNB * q0;
+            Ut[((ct / kNB) * h + kr) * kNB + (ct % kNB)] = su_val[e];
+          }
         }
         __syncthreads();
         // kSB rows per warp at a time (rows t = t0 + u * nwarps + warp, so the
         // longest rows stay spread over the warps): their loads of A go out
-        // together before any row's sum is formed
+        // together before any row's sums are formed
         constexpr int kSB = 8;
         for (int t0 = 0; t0 < d.n_srow; t0 += kSB * nwarps) {
-          T cur[kSB];
+          T cur[kSB][kPS];
           int ir[kSB], ro[kSB], rc[kSB];
 #pragma unroll
           for (int u = 0; u < kSB; ++u) {
@@ -535,7 +539,10 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
           }
 #pragma unroll
           for (int u = 0; u < kSB; ++u) {
-            cur[u] = (ir[u] >= 0 && lane < wq) ? A[(int64_t)(h + ir[u]) * ldm + c0 + lane] : T(0);
+            const T* Ai = A + (int64_t)(h + max(ir[u], 0)) * ldm + h + kNB * q0 + lane;
+#pragma unroll
+            for (int j = 0; j < kPS; ++j)
+              cur[u][j] = (ir[u] >= 0 && j < np && h + kNB * (q0 + j) + lane < n) ? Ai[kNB * j] : T(0);
             ro[u] = ir[u] >= 0 ? __ldg(d.lrhoff + ir[u]) : 0;
             rc[u] = ir[u] >= 0 ? __ldg(d.lrhead + ir[u]) : 0;
           }
@@ -543,14 +550,20 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
           for (int u = 0; u < kSB; ++u) {
             if (ir[u] < 0) continue;
             const int o = ro[u], cnt = rc[u];
-            T a0 = T(0), a1 = T(0);
-            int e = 0;
-            for (; e + 1 < cnt; e += 2) {
-              a0 += l21s[o + e] * Ut[(int)l21k[o + e] * kNB + lane];
-              a1 += l21s[o + e + 1] * Ut[(int)l21k[o + e + 1] * kNB + lane];
+            T acc[kPS];
+#pragma unroll
+            for (int j = 0; j < kPS; ++j) acc[j] = T(0);
+            for (int e = 0; e < cnt; ++e) {
+              const T l = l21s[o + e];
+              const T* ut = Ut + (int)l21k[o + e] * kNB + lane;
+#pragma unroll
+              for (int j = 0; j < kPS; ++j)
+                if (j < np) acc[j] += l * ut[j * h * kNB];
             }
-            if (e < cnt) a0 += l21s[o + e] * Ut[(int)l21k[o + e] * kNB + lane];
-            if (lane < wq) A[(int64_t)(h + ir[u]) * ldm + c0 + lane] = cur[u] - (a0 + a1);
+            T* Ai = A + (int64_t)(h + ir[u]) * ldm + h + kNB * q0 + lane;
+#pragma unroll
+            for (int j = 0; j < kPS; ++j)
+              if (j < np && h + kNB * (q0 + j) + lane < n) Ai[kNB * j] = cur[u][j] - acc[j];
           }
         }
         __syncthreads();
@@ -2062,7 +2075,8 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     // phases B and S: A11 (then the U12 panel tile), the compact L21 and the
     // staged U12 must not overlap (U12 is staged while A11 is still read)
     const size_t su_start = esz * (size_t)kNB * (pl.pitch + pl.upitch);
-    const size_t l21_off = ((std::max(a11, esz * (size_t)lu.head * kNB) + 15) / 16) * 16;
+    const size_t l21_off =
+        ((std::max(a11, esz * (size_t)lu.head * kNB * std::min(kPS, pl.n_panels)) + 15) / 16) * 16;
     const size_t l21_end = l21_off + (esz + 2) * (size_t)pl.n_l21;
     pl.l21_off = (int)l21_off;
     const size_t head_b = su_start + stage_u12;
