@@ -83,6 +83,8 @@ void release_all(sm_net* net) {
   lu.d_lrhk.release();
   lu.d_srow.release();
   net->d_jt_slot.release();
+  net->d_jdesc.release();
+  net->d_jlong.release();
   net->d_sc_ptr.release();
   net->d_sc_ent.release();
   lu.d_lptr.release();

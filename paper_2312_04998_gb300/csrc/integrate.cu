@@ -59,6 +59,9 @@ struct Dev {
   const int2 *jt_word, *jt_slot, *reac;
   const int* sc_ptr;
   const uint32_t* sc_ent;
+  const int4* jdesc;     // per Jacobian entry {t0, t1, jrc, row << 16 | col}
+  const int* jlong;      // entries with more than kJLong terms
+  int n_jlong;
 };
 
 __device__ __forceinline__ double& V(double* a, const Dev& d, int s, int64_t c) {
@@ -350,29 +353,42 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         wif[s] = (float)(1.0 / wv);
       }
     __syncthreads();
-    for (int p = tid; p < d.nnz_j; p += nthr) {
-      double acc = 0.0;
-      const int t0 = __ldg(d.jt_ptr + p), t1 = __ldg(d.jt_ptr + p + 1);
-      const int rc = __ldg(d.jrc + p);
-      int t = t0;
-      for (; t + 1 < t1; t += 2) {
-        const int2 wa = __ldg(d.jt_slot + t), wb = __ldg(d.jt_slot + t + 1);
-        acc = fma(coef[(uint32_t)wa.x >> 24], dR[2 * (wa.x & 0xFFFFFF) + wa.y], acc);
-        acc = fma(coef[(uint32_t)wb.x >> 24], dR[2 * (wb.x & 0xFFFFFF) + wb.y], acc);
-      }
-      if (t < t1) {
-        const int2 wa = __ldg(d.jt_slot + t);
-        acc = fma(coef[(uint32_t)wa.x >> 24], dR[2 * (wa.x & 0xFFFFFF) + wa.y], acc);
-      }
-      const int pi = rc >> 16, pj = rc & 0xFFFF;
+    // M_ij = delta_ij - gamma sum_terms coef dR, stored in elimination order
+    // (W M W^-1 with this step's error weights, scaled in FP32, when mixed)
+    auto store_m = [&](const int4 ds, double acc) {
+      const int pi = ds.z >> 16, pj = ds.z & 0xFFFF;
       const double m = fma(-gamma, acc, pi == pj ? 1.0 : 0.0);
       T* dst = A + (int64_t)pi * ldm + pj;
-      if (d.mixed) {
-        // W M W^-1 with the error weights of this step (scaling in FP32)
-        *dst = T((float)m * (wsf[__ldg(d.perm + pi)] * wif[__ldg(d.perm + pj)]));
-      } else {
-        *dst = T(m);
+      if (d.mixed) *dst = T((float)m * (wsf[ds.w >> 16] * wif[ds.w & 0xFFFF]));
+      else *dst = T(m);
+    };
+    auto term = [&](double acc, int t) {
+      const int2 w = __ldg(d.jt_slot + t);
+      return fma(coef[(uint32_t)w.x >> 24], dR[2 * (w.x & 0xFFFFFF) + w.y], acc);
+    };
+    // entries with more than kJLong terms (the hub species'): a warp each
+    for (int q = warp; q < d.n_jlong; q += nwarps) {
+      const int4 ds = __ldg(d.jdesc + __ldg(d.jlong + q));
+      double acc = 0.0;
+      for (int t = ds.x + lane; t < ds.y; t += 32) acc = term(acc, t);
+      acc = warp_sum(acc);
+      if (lane == 0) store_m(ds, acc);
+    }
+    // the others: a thread each, two entries at a time so that their loads
+    // overlap
+    for (int p = tid; p < d.nnz_j; p += 2 * nthr) {
+      const bool hb = p + nthr < d.nnz_j;
+      const int4 da = __ldg(d.jdesc + p);
+      const int4 db = hb ? __ldg(d.jdesc + p + nthr) : make_int4(0, 0, 0, 0);
+      const bool la = da.y - da.x <= kJLong, lb = hb && db.y - db.x <= kJLong;
+      double aa = 0.0, ab = 0.0;
+      const int na = la ? da.y - da.x : 0, nb = lb ? db.y - db.x : 0;
+      for (int u = 0; u < max(na, nb); ++u) {
+        if (u < na) aa = term(aa, da.x + u);
+        if (u < nb) ab = term(ab, db.x + u);
       }
+      if (la) store_m(da, aa);
+      if (lb) store_m(db, ab);
     }
     __syncthreads();
     // ---- phase B: sparse head
@@ -2025,6 +2041,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.n_srow = (int)lu.srow.size();
   d.jt_slot = net->d_jt_slot.as<int2>(); d.reac = net->d_reac.as<int2>();
   d.sc_ptr = net->d_sc_ptr.as<int>(); d.sc_ent = net->d_sc_ent.as<uint32_t>();
+  d.jdesc = net->d_jdesc.as<int4>(); d.jlong = net->d_jlong.as<int>(); d.n_jlong = (int)net->jlong.size();
   d.jp_ptr = net->d_jp_ptr.as<int>(); d.jt_ptr = net->d_jt_ptr.as<int>();
   d.jt_word = net->d_jt_word.as<int2>(); d.jpos = lu.d_jpos.as<int>();
   d.record = o.record_steps > 0 ? o.record_steps : 0;

@@ -10,6 +10,9 @@
 
 #include "stoich.h"
 
+// Jacobian entries with more terms than this are gathered by a whole warp.
+constexpr int kJLong = 32;
+
 // Device status word bits written by kernels (never trap).
 enum : int32_t {
   DEV_ERR_NONE = 0,
@@ -106,6 +109,8 @@ struct sm_net {
   DevArray d_rate;        // RatePar per reaction: (log alpha | alpha, beta, gamma, class)
   DevArray d_jp_ptr, d_jt_ptr, d_jt_word;  // Jacobian gather lists
   DevArray d_jt_slot;                      // (reaction | coef << 24, reactant slot) per term
+  std::vector<int32_t> jlong;              // Jacobian entries with more than kJLong terms
+  DevArray d_jdesc, d_jlong;               // per entry {t0, t1, jrc, row << 16 | col}; long entries
   DevArray d_sc_ptr, d_sc_ent;             // S by columns: pointers and (species | coef << 24)
   std::vector<int32_t> jchunk;             // J entries per gather chunk (balanced by terms)
   DevArray d_jchunk;

@@ -654,6 +654,25 @@ sm_status net_upload(sm_net* net) {
   if (!lu.ucidx.empty() && (st = lu.d_ucidx.upload(lu.ucidx.data(), lu.ucidx.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_jpos.upload(lu.jpos.data(), lu.jpos.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_jrc.upload(lu.jrc.data(), lu.jrc.size() * 4)) != SM_OK) return st;
+  // one 16-byte descriptor per Jacobian entry for the refresh gather: term
+  // range, (row, column) in elimination order, (row, column) species; and
+  // the entries with more than kJLong terms, which a warp gathers
+  {
+    const size_t n_e = net->jp_col.size();
+    std::vector<int32_t> desc(4 * n_e);
+    net->jlong.clear();
+    for (int32_t i = 0; i < net->n_s; ++i)
+      for (int32_t e = net->jp_ptr[i]; e < net->jp_ptr[i + 1]; ++e) {
+        desc[4 * e] = net->jt_ptr[e];
+        desc[4 * e + 1] = net->jt_ptr[e + 1];
+        desc[4 * e + 2] = lu.jrc[e];
+        desc[4 * e + 3] = (i << 16) | net->jp_col[e];
+        if (net->jt_ptr[e + 1] - net->jt_ptr[e] > kJLong) net->jlong.push_back(e);
+      }
+    if ((st = net->d_jdesc.upload(desc.data(), desc.size() * 4)) != SM_OK) return st;
+    if (!net->jlong.empty() && (st = net->d_jlong.upload(net->jlong.data(), net->jlong.size() * 4)) != SM_OK)
+      return st;
+  }
   if (!lu.uoff.empty() && (st = lu.d_uoff.upload(lu.uoff.data(), lu.uoff.size() * 4)) != SM_OK) return st;
   if (!lu.lrhead.empty() && (st = lu.d_lrhead.upload(lu.lrhead.data(), lu.lrhead.size() * 4)) != SM_OK)
     return st;
