@@ -216,22 +216,37 @@ __global__ void predict_kernel(Dev d) {
   d.m_it[c] = 0;
   d.dprev[c] = 0.0;
   if (refresh) d.list[atomicAdd(&d.counters[0], 1)] = (int)c;
-  for (int s = 0; s < d.n; ++s) {
-    const int64_t o = (int64_t)s * d.ld + c;
-    const double y0 = Yh(d, 0)[o];
-    double yp;
-    if (nh == 1) {
-      yp = y0 + h * d.f0[o];
-    } else {
-      yp = 0.0;
-      for (int i = 0; i <= q; ++i) yp += wts[i] * Yh(d, i)[o];
+  // kPU species at a time with the history loops unrolled, so that each
+  // thread has kPU * (q + 1) loads in flight (one thread per cell leaves too
+  // few warps to cover the memory latency otherwise)
+  constexpr int kPU = 4;
+  const bool euler = nh == 1;
+  for (int s0 = 0; s0 < d.n; s0 += kPU) {
+    double Yv[kPU][QMAX + 1], fv[kPU];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int64_t o = (int64_t)(s0 + u) * d.ld + c;
+      const bool live = s0 + u < d.n;
+#pragma unroll
+      for (int i = 0; i <= QMAX; ++i) Yv[u][i] = (live && i <= q && i < nh) ? Yh(d, i)[o] : 0.0;
+      fv[u] = (live && euler) ? d.f0[o] : 0.0;
     }
-    double ps = 0.0;
-    for (int i = 1; i <= q; ++i) ps += al[i] * Yh(d, i - 1)[o];
-    d.ypred[o] = yp;
-    d.y[o] = yp;
-    d.psi[o] = ps;
-    d.w[o] = 1.0 / (d.rtol * fabs(y0) + d.atol);
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      if (s0 + u >= d.n) break;
+      const int64_t o = (int64_t)(s0 + u) * d.ld + c;
+      const double y0 = Yv[u][0];
+      double yp = euler ? y0 + h * fv[u] : 0.0, ps = 0.0;
+#pragma unroll
+      for (int i = 0; i <= QMAX; ++i) {
+        if (!euler && i <= q) yp += wts[i] * Yv[u][i];
+        if (i >= 1 && i <= q) ps += al[i] * Yv[u][i - 1];
+      }
+      d.ypred[o] = yp;
+      d.y[o] = yp;
+      d.psi[o] = ps;
+      d.w[o] = 1.0 / (d.rtol * fabs(y0) + d.atol);
+    }
   }
 }
 
@@ -1005,6 +1020,7 @@ __global__ void finish_kernel(Dev d) {
   double T[QMAX + 1];
   for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
   double acc = 0.0;
+#pragma unroll 8
   for (int s = 0; s < n; ++s) {
     const int64_t o = (int64_t)s * d.ld + c;
     const double v = (d.y[o] - d.ypred[o]) * d.w[o];
@@ -1042,12 +1058,15 @@ __global__ void finish_kernel(Dev d) {
       double wl[QMAX + 1];
       if (lo) lagrange(T, q, tnew, wl);
       double acc_lo = 0.0, acc_hi = 0.0;
+#pragma unroll 4
       for (int s = 0; s < n; ++s) {
         const int64_t o = (int64_t)s * d.ld + c;
         const double yv = d.y[o], wv = d.w[o];
         if (lo) {
           double p = 0.0;
-          for (int i = 0; i < q; ++i) p += wl[i] * Yh(d, i)[o];
+#pragma unroll
+          for (int i = 0; i < QMAX; ++i)
+            if (i < q) p += wl[i] * Yh(d, i)[o];
           const double v = (yv - p) * wv;
           acc_lo += v * v;
         }
@@ -1077,11 +1096,18 @@ __global__ void finish_kernel(Dev d) {
   // commit: shift the history, newest first
   const int nh_new = min(nh + 1, d.q_max + 1);
   const bool keep_e = best_q == q;
+#pragma unroll 4
   for (int s = 0; s < n; ++s) {
     const int64_t o = (int64_t)s * d.ld + c;
-    for (int i = nh_new - 1; i >= 1; --i) Yh(d, i)[o] = Yh(d, i - 1)[o];
+    double Yv[QMAX];
+#pragma unroll
+    for (int i = 0; i < QMAX; ++i) Yv[i] = i < nh_new - 1 ? Yh(d, i)[o] : 0.0;
     const double yv = d.y[o];
-    if (keep_e) d.eprev[o] = yv - d.ypred[o];
+    const double yp = keep_e ? d.ypred[o] : 0.0;
+#pragma unroll
+    for (int i = 0; i < QMAX; ++i)
+      if (i < nh_new - 1) Yh(d, i + 1)[o] = Yv[i];
+    if (keep_e) d.eprev[o] = yv - yp;
     Yh(d, 0)[o] = yv;
   }
   for (int i = nh_new - 1; i >= 1; --i) d.tn[(int64_t)i * d.ld + c] = T[i - 1];
