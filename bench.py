@@ -42,7 +42,7 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "tf32", "fp64"])
     p.add_argument("--cells", type=int, default=65536)
     p.add_argument("--t-end-yr", type=float, default=1e6)
     p.add_argument("--time-kernel", default="refresh",
@@ -427,7 +427,7 @@ def main():
     if per_launch_flops is not None:
         avg_s = kern_ms * 1e-3 / kern_n
         ach = per_launch_flops / avg_s / 1e12
-        fp32 = a.precision == "mixed" and a.time_kernel == "refresh"
+        fp32 = a.precision != "fp64" and a.time_kernel == "refresh"
         pk = peak_fp32 if fp32 else peak_fp64
         roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": TRAFFIC.get((a.time_kernel, a.precision, kernel_source_hash())),
@@ -435,7 +435,7 @@ def main():
                 "avg_launch_ms": kern_ms / kern_n, "timed_launches": kern_n,
                 "peak_source": "unit counts x 2.07 GHz max SM clock: FP32 152x128x2, FP64 152x4 flops/clk"}
     fp64 = None
-    if a.fp64_cells > 0 and a.precision == "mixed":
+    if a.fp64_cells > 0 and a.precision != "fp64":
         n = min(a.fp64_cells, C)
         fp64 = fp64_comparison(B, net, d, T[:n], nH[:n], Av[:n], np.ascontiguousarray(y0[:, :n]), t_end, dev)
     del state
@@ -450,7 +450,7 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f64+f32",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32", "tf32": "f64+f32+tf32"}[a.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells_per_gpu": C, "n_s": d.n_s, "n_r": d.n_r,
                    "t_end_yr": a.t_end_yr, "rtol": 1e-6, "atol": 1e-20, "precision": a.precision,

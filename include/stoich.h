@@ -203,9 +203,14 @@ sm_status sm_jac_eval(const sm_net* net, int64_t C, const double* d_k, const dou
  * The Newton matrix is factorised without pivoting in a minimum-degree order
  * (as DLSODES's sparse solver does); SM_PREC_FP64 factorises and solves in
  * FP64, SM_PREC_MIXED in FP32 on the WRMS-equilibrated matrix W M W^-1
- * while the residual, Jacobian and all state stay FP64.
+ * while the residual, Jacobian and all state stay FP64; SM_PREC_TF32 is
+ * SM_PREC_MIXED with the dense trailing block's updates on the tensor cores
+ * (each operand split into TF32 high and low parts, three products per pair,
+ * FP32 accumulation: FP32-level accuracy).  In both reduced precisions
+ * each Newton iteration forms an FP64 residual, so the iteration refines the
+ * low-precision solve.
  * ------------------------------------------------------------------------ */
-enum { SM_PREC_FP64 = 0, SM_PREC_MIXED = 1 };
+enum { SM_PREC_FP64 = 0, SM_PREC_MIXED = 1, SM_PREC_TF32 = 2 };
 
 typedef struct {
     double rtol, atol;        /* error weights 1/(rtol |y| + atol)                 */
@@ -218,7 +223,7 @@ typedef struct {
     int32_t j_age_max;        /* accepted steps between Jacobian refreshes         */
     int32_t newton_max;       /* Newton iterations per attempt, 1..8               */
     int32_t max_conv_fails;   /* consecutive Newton failures before SM_CELL_CONV   */
-    int32_t precision;        /* SM_PREC_FP64 or SM_PREC_MIXED                     */
+    int32_t precision;        /* SM_PREC_FP64, SM_PREC_MIXED or SM_PREC_TF32       */
     int32_t use_graph;        /* capture the attempt loop in a CUDA graph (1) or not */
     int32_t attempts_per_sync;/* attempts launched between completion checks      */
     int32_t timing_kind;      /* SM_TIME_*: kernel class timed with CUDA events    */
@@ -338,7 +343,7 @@ sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, 
  * history): read the solution first, and call sm_state_init or sm_integrate
  * before stepping again; recorded steps and sm_cell_stats stay valid.
  * Errors: SM_EINVAL (bad arguments, or the state records nothing),
- * SM_ENOTSUP (a state created with SM_PREC_MIXED: the adjoint runs in FP64
+ * SM_ENOTSUP (a state created with SM_PREC_MIXED or SM_PREC_TF32: the adjoint runs in FP64
  * only), SM_ENOMEM (workspace does not fit: use a smaller cells_per_pass);
  * SM_EPARTIAL if any cell's d_astat is not 0.  Synchronises the host with the
  * state's stream once per pass. */

@@ -60,7 +60,7 @@ CELL_STATS_DTYPE = np.dtype([("status", np.int32), ("steps", np.int32), ("reject
                              ("conv_fails", np.int32), ("newton_iters", np.int32),
                              ("jac_evals", np.int32), ("q_last", np.int32), ("pad", np.int32),
                              ("t", np.float64), ("h", np.float64)])
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "tf32": 2}
 TIME = {"none": 0, "refresh": 1, "rhs": 2, "solve": 3, "predict": 4, "finish": 5}
 CELL_OK, CELL_MAXSTEPS, CELL_HMIN, CELL_CONV, CELL_NAN, CELL_RUNNING = range(6)
 

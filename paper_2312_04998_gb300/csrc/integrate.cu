@@ -32,7 +32,7 @@ enum : int {
 };
 
 struct Dev {
-  int n, n_r, nnz_j, mixed, head;
+  int n, n_r, nnz_j, mixed, tf32, head;
   int64_t C, ld;
   double rtol, atol, gamma_tol, newton_tol, eta_max, eta_keep, t_end;
   int q_max, max_steps, j_age_max, newton_max, max_conv_fails;
@@ -310,6 +310,89 @@ template <> struct Vec4<double> {
 };
 
 template <class T> __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Tensor-core trailing update C -= L U with K = kNB for the FP32 factors
+// (precision mode TF32): L (r x kNB) column-major in shared memory (element
+// (i, k) at L[k * pl + i]), U (kNB x r) row-major (element (k, j) at U[k * pu
+// + j]), C (r x r) in global memory with row stride ldc.  One warp per 32 x 32
+// tile of C: 2 x 4 mma.m16n8k8 TF32 fragments, each operand split into TF32
+// high and low parts (three products per pair: FP32-level accuracy), FP32
+// accumulators loaded from and stored back to C.  Fragment layouts of m16n8k8 .tf32 (g = lane / 4,
+// t = lane % 4): A {(g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)}, B {(t, g),
+// (t + 4, g)}, C {(g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1)}.  Rows
+// and columns of a tile past r read whatever follows in shared memory and are
+// neither loaded from nor stored to C.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return u;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ void tf32_trailing_update(float* C, int ldc, int r, const float* L, int pl, const float* U, int pu,
+                                     int warp, int nwarps, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int nb = (r + 31) / 32;
+  for (int tile = warp; tile < nb * nb; tile += nwarps) {
+    const int i0 = (tile / nb) * 32, j0 = (tile % nb) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = i0 + mt * 16 + g + (e >> 1) * 8, col = j0 + nt * 8 + 2 * t + (e & 1);
+          acc[mt][nt][e] = (row < r && col < r) ? C[(int64_t)row * ldc + col] : 0.f;
+        }
+#pragma unroll
+    for (int k0 = 0; k0 < kNB; k0 += 8) {
+      // each operand x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the
+      // products hi*hi + hi*lo + lo*hi keep FP32-level accuracy
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+      const float* l0 = L + (k0 + t) * pl + i0 + g;
+      const float* l4 = l0 + 4 * pl;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const float v[4] = {-l0[mt * 16], -l0[mt * 16 + 8], -l4[mt * 16], -l4[mt * 16 + 8]};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(v[e], ah[mt][e], al[mt][e]);
+      }
+      const float* u0 = U + (k0 + t) * pu + j0 + g;
+      const float* u4 = u0 + 4 * pu;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        split_tf32(u0[nt * 8], bh[nt][0], bl[nt][0]);
+        split_tf32(u4[nt * 8], bh[nt][1], bl[nt][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          mma_tf32(acc[mt][nt], al[mt], bh[nt]);
+          mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
+          mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = i0 + mt * 16 + g + (e >> 1) * 8, col = j0 + nt * 8 + 2 * t + (e & 1);
+          if (row < r && col < r) C[(int64_t)row * ldc + col] = acc[mt][nt][e];
+        }
+  }
+}
 
 template <class T>
 __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, const double* __restrict__ k,
@@ -719,8 +802,16 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         for (int a = warp; a < w; a += nwarps)
           for (int b = lane; b < r; b += 32) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * upitch + b];
         // A22 -= L21 U12; L21 column kk is Pt[kk * pitch + w + i]
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+          if (d.tf32 && w == kNB) {
+            tf32_trailing_update(A + (int64_t)(p0 + w) * ldm + p0 + w, ldm, r, Pt + w, pitch, U, upitch, warp,
+                                 nwarps, lane);
+            done = true;
+          }
+        }
         const int ty = tid / 16, tx = tid % 16;
-        for (int t0 = 0; t0 < r; t0 += kBM)
+        for (int t0 = 0; t0 < (done ? 0 : r); t0 += kBM)
           for (int u0 = 0; u0 < r; u0 += kBN) {
             const int i0 = t0 + ty * kTM, j0 = u0 + tx * kTN;
             if (i0 >= r || j0 >= r) continue;
@@ -1572,7 +1663,8 @@ bool opts_ok(const sm_opts& o) {
   return o.rtol >= 0.0 && o.atol > 0.0 && o.gamma_tol > 0.0 && o.newton_tol > 0.0 && o.eta_max >= 1.0 &&
          o.eta_keep >= 1.0 && o.q_max >= 1 && o.q_max <= QMAX && o.max_steps >= 1 && o.j_age_max >= 1 &&
          o.newton_max >= 1 && o.newton_max <= 8 && o.max_conv_fails >= 1 &&
-         (o.precision == SM_PREC_FP64 || o.precision == SM_PREC_MIXED) && o.attempts_per_sync >= 1 &&
+         (o.precision == SM_PREC_FP64 || o.precision == SM_PREC_MIXED || o.precision == SM_PREC_TF32) &&
+         o.attempts_per_sync >= 1 &&
          o.timing_kind >= SM_TIME_NONE && o.timing_kind <= SM_TIME_FINISH && o.record_steps >= 0;
 }
 
@@ -1673,7 +1765,7 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
 sm_status enqueue_group(sm_state* st, const double* k, int64_t ldk, int attempts, cudaStream_t s) {
   if (!st->opts.use_graph) st->ev_used = 0;
   for (int a = 0; a < attempts; ++a) {
-    sm_status r = st->opts.precision == SM_PREC_MIXED ? enqueue_attempt<float>(st, k, ldk, s)
+    sm_status r = st->opts.precision != SM_PREC_FP64 ? enqueue_attempt<float>(st, k, ldk, s)
                                                       : enqueue_attempt<double>(st, k, ldk, s);
     if (r != SM_OK) return r;
   }
@@ -2005,7 +2097,8 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.n = n;
   d.n_r = net->n_r;
   d.nnz_j = (int)net->jp_col.size();
-  d.mixed = o.precision == SM_PREC_MIXED;
+  d.mixed = o.precision != SM_PREC_FP64;
+  d.tf32 = o.precision == SM_PREC_TF32;
   d.C = C;
   d.ld = ld;
   d.rtol = o.rtol;
@@ -2098,9 +2191,14 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     // shared memory of the refresh kernel: the largest of its three phases
     RefreshPlan& pl = st->plan;
     const int nt = n - lu.head;
-    pl.pitch = round_up(nt + 4, 4);  // rows past the panel height: zero padding for 4-wide loads
+    // rows past the panel height: zero padding for 4-wide loads; both pitches
+    // are 8 mod 32 words so that the tensor-core fragment loads (4 k-rows x 8
+    // columns per instruction) fall in 32 distinct banks
+    pl.pitch = round_up(nt + 4, 4);
+    while (pl.pitch % 32 != 8) pl.pitch += 4;
     pl.n_panels = (nt + kNB - 1) / kNB;
     pl.upitch = round_up(std::max(nt - kNB, 4), 4);
+    while (pl.upitch % 32 != 8) pl.upitch += 4;
     pl.n_l21 = lu.lrhoff.empty() ? 0 : lu.lrhoff.back();
     pl.n_u12 = 0;
     for (int k2 = 0; k2 < lu.head; ++k2) pl.n_u12 += lu.uptr[k2 + 1] - lu.uoff[(size_t)k2 * (pl.n_panels + 1)];

@@ -66,7 +66,7 @@ def riccati_B(t, kk, z, A0, B0):
     return (B2 * inv_r - B1) / (inv_r - 1.0)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
 def test_worked_example_riccati(torch, B, precision):
     """2A -> B, B -> 2A (Eqs. 2-6) integrated per cell with different k and
     end times folded into one batch, against the exact solution."""
@@ -107,11 +107,13 @@ def small_case():
     return d, k, y0, t_end, ref, load_truth("small")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
 def test_small_network_matches_oracle(torch, B, small_case, precision):
     """The GPU solution is no farther from the tight-tolerance truth than twice
     the oracle's own rtol-1e-6 solution is (both run the same method at the
-    same tolerance; their global errors, a few tolerance units, set the bar)."""
+    same tolerance; their global errors, a few tolerance units, set the bar).
+    The reduced precisions (FP32 factors, with TF32 trailing updates in the
+    tf32 mode) take the mixed bar."""
     d, k, y0, t_end, ref, truth = small_case
     y, stats, code = run_gpu(torch, B, d, k, y0, t_end, precision=precision)
     assert code == B.SM_OK, stats["status"]
@@ -153,7 +155,7 @@ def moderate_case():
 
 
 @pytest.mark.parametrize("case", ["moderate", "stiff"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
 def test_conservation_gpu(torch, B, small_case, moderate_case, case, precision):
     """Element totals and charge through integration.  In exact arithmetic
     every Newton correction conserves them (E S = 0 makes E M = E); in
@@ -208,7 +210,7 @@ def test_max_steps_reported(torch, B):
     assert np.all(stats["status"] == B.CELL_MAXSTEPS) and np.all(stats["steps"] == 5)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
 def test_large_network_matches_oracle(torch, B, precision):
     """4 cells of the 470 x 6000 network to 1e6 yr against the stored
     rtol-1e-10 truth; the bar is the oracle's own rtol-1e-6 distance to it
@@ -223,8 +225,16 @@ def test_large_network_matches_oracle(torch, B, precision):
     e_g = weighted_err(y, truth)
     factor = 2.0 if precision == "fp64" else 4.0
     assert e_g <= factor * max(e_o, 1.0), (e_g, e_o)
+    # element totals: the same bars as the conservation test (the oracle's
+    # own drift, from its stored rtol-1e-6 solution, for FP64)
     E = on.element_matrix(d).astype(float)
-    assert np.allclose(E[:3] @ y, E[:3] @ y0, rtol=1e-12)
+    tot0 = np.abs(E[:3] @ y0)
+    drift = (np.abs(E[:3] @ y - E[:3] @ y0) / tot0).max(axis=1)
+    if precision == "fp64":
+        drift_o = (np.abs(E[:3] @ yo - E[:3] @ y0) / tot0).max(axis=1)
+        assert np.all(drift <= 4.0 * np.maximum(drift_o, 1e-13)), (drift, drift_o)
+    else:
+        assert np.all(drift <= 1e-4), drift
 
 
 def test_state_reuse_with_new_end_time(torch, B):
