@@ -1608,8 +1608,8 @@ struct sm_state {
   Dev d{};
   DevArray scal_d, scal_i, vec, lu, list, counters, scratch, rec_d, rec_i;
   DevArray adj_d, adj_i, adj_lu;   // sm_adjoint workspace, grown on demand
-  cudaStream_t s = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t s = nullptr, s2 = nullptr;          // s2: second half of the Newton rounds
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
   int* h_counters = nullptr;  // pinned
   cudaGraphExec_t graph = nullptr;
   const double* graph_k = nullptr;
@@ -1687,6 +1687,9 @@ void free_state(sm_state* st) {
   if (st->h_counters) cudaFreeHost(st->h_counters);
   if (st->ev_in) cudaEventDestroy(st->ev_in);
   if (st->ev_out) cudaEventDestroy(st->ev_out);
+  if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+  if (st->ev_join) cudaEventDestroy(st->ev_join);
+  if (st->s2) cudaStreamDestroy(st->s2);
   if (st->s) cudaStreamDestroy(st->s);
 }
 
@@ -1729,7 +1732,10 @@ void harvest_times(sm_state* st) {
   }
 }
 
-constexpr int kLaunchesFixed = 3;  // predict, refresh, finish (+3 per Newton round)
+Dev shift_cells(const Dev& d0, int64_t c0, int64_t Cc);
+
+constexpr int kLaunchesFixed = 3;  // predict, refresh, finish (+3 per Newton round and half)
+constexpr int64_t kSplitMin = 2048; // smallest half worth a second stream
 
 template <class T>
 sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream_t s) {
@@ -1744,21 +1750,42 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(d, k, ldk, st->plan);
   if ((r = time_mark(st, SM_TIME_REFRESH, false, s)) != SM_OK) return r;
   const size_t smem = sizeof(T) * (size_t)kSolveWarps * ((d.n + 3) / 4 * 4);
-  for (int m = 0; m < d.newton_max; ++m) {
-    if ((r = time_mark(st, SM_TIME_RHS, true, s)) != SM_OK) return r;
-    r = launch_rhs_masked(net, d.C, k, ldk, d.y, d.f, d.ld, st->scratch.as<double>(), d.ld, d.flags,
-                          F_NEWTON, s);
-    if (r != SM_OK) return r;
-    if ((r = time_mark(st, SM_TIME_RHS, false, s)) != SM_OK) return r;
-    if ((r = time_mark(st, SM_TIME_SOLVE, true, s)) != SM_OK) return r;
-    solve_update_kernel<T><<<blocks(d.C, kSolveWarps), 32 * kSolveWarps, smem, s>>>(d, F_NEWTON, F_NEWTON);
-    if ((r = time_mark(st, SM_TIME_SOLVE, false, s)) != SM_OK) return r;
+  // Newton rounds.  Unless the RHS or solve class is being timed, the cells
+  // are split into two halves whose rounds run on two streams: the RHS
+  // (FP64-pipe bound) of one half overlaps the substitution (bandwidth
+  // bound) of the other.
+  const bool split = st->opts.timing_kind != SM_TIME_RHS && st->opts.timing_kind != SM_TIME_SOLVE &&
+                     d.C >= 2 * kSplitMin;
+  const int64_t ch = split ? (d.C / 2 + 31) / 32 * 32 : d.C;
+  if (split) {
+    SM_TRY_CUDA(cudaEventRecord(st->ev_fork, s));
+    SM_TRY_CUDA(cudaStreamWaitEvent(st->s2, st->ev_fork, 0));
+  }
+  for (int half = 0; half < (split ? 2 : 1); ++half) {
+    const int64_t c0 = half * ch, cn = split ? (half ? d.C - ch : ch) : d.C;
+    cudaStream_t hs = half ? st->s2 : s;
+    Dev dh = shift_cells(d, c0, cn);
+    dh.lu = static_cast<T*>(d.lu) + c0 * d.lu_stride;
+    for (int m = 0; m < d.newton_max; ++m) {
+      if ((r = time_mark(st, SM_TIME_RHS, true, hs)) != SM_OK) return r;
+      r = launch_rhs_masked(net, cn, k + c0, ldk, dh.y, dh.f, d.ld, st->scratch.as<double>() + c0, d.ld,
+                            dh.flags, F_NEWTON, hs);
+      if (r != SM_OK) return r;
+      if ((r = time_mark(st, SM_TIME_RHS, false, hs)) != SM_OK) return r;
+      if ((r = time_mark(st, SM_TIME_SOLVE, true, hs)) != SM_OK) return r;
+      solve_update_kernel<T><<<blocks(cn, kSolveWarps), 32 * kSolveWarps, smem, hs>>>(dh, F_NEWTON, F_NEWTON);
+      if ((r = time_mark(st, SM_TIME_SOLVE, false, hs)) != SM_OK) return r;
+    }
+  }
+  if (split) {
+    SM_TRY_CUDA(cudaEventRecord(st->ev_join, st->s2));
+    SM_TRY_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
   }
   if ((r = time_mark(st, SM_TIME_FINISH, true, s)) != SM_OK) return r;
   finish_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_FINISH, false, s)) != SM_OK) return r;
   SM_TRY_CUDA(cudaGetLastError());
-  st->launches += kLaunchesFixed + 3 * d.newton_max;
+  st->launches += kLaunchesFixed + 3 * d.newton_max * (split ? 2 : 1);
   return SM_OK;
 }
 
@@ -2182,6 +2209,9 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   if (cudaStreamCreateWithFlags(&st->s, cudaStreamNonBlocking) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
+  if (cudaStreamCreateWithFlags(&st->s2, cudaStreamNonBlocking) != cudaSuccess) return fail(SM_ECUDA);
+  if (cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
+  if (cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaMallocHost(&st->h_counters, 4 * sizeof(int)) != cudaSuccess) return fail(SM_ENOMEM);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device);

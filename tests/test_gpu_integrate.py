@@ -261,3 +261,22 @@ def test_state_reuse_with_new_end_time(torch, B):
         assert np.all(s["t"] == 1e5 * YEAR)
         out.append((yd.cpu().numpy(), s["steps"].copy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_split_newton_rounds_are_bit_identical(torch, B, precision):
+    """From 4096 cells on, the Newton rounds of the two halves of the batch run
+    on two streams (unless the solve or RHS class is being timed); the result must be
+    the same bits as the single-stream rounds."""
+    d = sn.generate(2312, 32, 180)
+    C = 4200
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
+    k = ok.rate_coefficients(d, T, nH, Av)
+    y0 = sc.atomic_start(d, C)
+    out = []
+    for timing in ("none", "solve"):
+        y, stats, code = run_gpu(torch, B, d, k, y0, 1e3 * YEAR, precision=precision, timing_kind=timing)
+        assert code == B.SM_OK
+        out.append((y, stats["steps"].copy(), stats["newton_iters"].copy()))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
