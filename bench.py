@@ -54,6 +54,9 @@ def args_():
                    help="cells of the plain FP64 comparison integrate (0 = skip)")
     p.add_argument("--adjoint-cells", type=int, default=1024,
                    help="cells of the adjoint/forward measurement (0 = skip)")
+    p.add_argument("--rhs-cells", type=int, default=4096,
+                   help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
+    p.add_argument("--rhs-only", action="store_true", help="run only the format grid and print it")
     return p.parse_args()
 
 
@@ -228,6 +231,72 @@ def fp64_comparison(B, net, d, T, nH, Av, y0, t_end, dev):
             "steps_per_cell": float(s["steps"].mean()), "cells_ok": int((s["status"] == 0).sum())}
 
 
+RHS_GRID = [("crs", "none", 1, 1), ("crs", "nnz", 1, 1), ("crs", "rcm", 1, 1), ("coo", "none", 1, 1),
+            ("coo", "rcm", 1, 1), ("ccs", "none", 1, 1), ("ccs", "rcm", 1, 1), ("sell", "none", 4, 1),
+            ("sell", "nnz", 8, 64), ("sell", "none", 32, 470), ("sell", "rcm", 8, 64)]
+
+
+def rhs_jac_grid(B, C, dev, peaks):
+    """rhs_eval for every storage format x row order of the grid and jac_eval,
+    on the RHS workload (470 x 6000, C cells, log-uniform abundances): median
+    of 20 CUDA-event-timed calls, L2 flushed (256 MB write) before each.
+    Algorithmic bytes and FP64 flops per cell come from sm_net_get_info."""
+    import numpy as np
+    import torch
+    from synth.workloads import make
+    d, T, nH, Av, y = make("rhs_jac_470x6000_c4096", cells=C)
+    net = B.Network(d, dev.index or 0)
+    info = net.info()
+    kd, yd = gpu_inputs(B, net, d, T, nH, Av, y, dev)
+    fd = torch.empty_like(yd)
+    Jd = torch.empty((info["nnz_J"], yd.shape[1]), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.int8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def med(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            ts.append(timed(fn, stream)[1])
+        return float(np.median(ts))
+
+    def row(kind, ms, nbytes, flops):
+        gbs = nbytes * C / (ms * 1e-3) / 1e9
+        tf = flops * C / (ms * 1e-3) / 1e12
+        return {"kind": kind, "us": ms * 1e3, "GB_s": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                "fp64_TF_s": tf, "fp64_frac": tf / peaks["fp64_tflops"]}
+
+    out = []
+    for fmt in RHS_GRID:
+        net.set_format(*fmt)
+        ms = med(lambda: net.rhs_eval(kd, yd, fd, C))
+        out.append(row("rhs " + "/".join(str(x) for x in fmt), ms, info["rhs_bytes"], info["rhs_flops"]))
+    net.set_format("crs", "none", 1, 1)
+    ms = med(lambda: net.jac_eval(kd, yd, Jd, C))
+    out.append(row("jac", ms, info["jac_bytes"], info["jac_flops"]))
+    net.sync()
+    net.close()
+    return {"workload": "rhs_jac_470x6000_c4096", "cells": C, "l2": "flushed before every call",
+            "rhs_bytes_per_cell": info["rhs_bytes"], "rhs_flops_per_cell": info["rhs_flops"],
+            "jac_bytes_per_cell": info["jac_bytes"], "jac_flops_per_cell": info["jac_flops"],
+            "peaks": peaks, "rows": out}
+
+
+def measured_peaks():
+    """HBM copy bandwidth from the measured-peaks file when present; the FP64
+    rate is our own FMA probe (1.19 TFLOP/s on this machine's GB300)."""
+    hbm = 6790.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mp = json.load(fh)
+        hbm = float(mp.get("hbm_gbs", hbm))
+    except (OSError, ValueError):
+        pass
+    return {"hbm_gbs": hbm, "fp64_tflops": 1.19}
+
+
 def adjoint_measurement(B, C, dev):
     """Discrete adjoint on the adjoint workload (470 x 6000, 1e5 yr, FP64,
     checkpoints every 16 steps): one recorded forward integrate and one reverse
@@ -297,6 +366,10 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if a.rhs_only:
+        if rank == 0:
+            print(json.dumps(rhs_jac_grid(B, a.rhs_cells, dev, measured_peaks())))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
@@ -440,6 +513,7 @@ def main():
         fp64 = fp64_comparison(B, net, d, T[:n], nH[:n], Av[:n], np.ascontiguousarray(y0[:, :n]), t_end, dev)
     del state
     adj = adjoint_measurement(B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
+    rhs = rhs_jac_grid(B, a.rhs_cells, dev, measured_peaks()) if a.rhs_cells > 0 else None
     cpu = None
     if not a.no_cpu:
         n = a.cpu_cells or host_cores()
@@ -462,7 +536,7 @@ def main():
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64": fp64, "adjoint": adj,
+        "fp64": fp64, "adjoint": adj, "rhs_jac": rhs,
     }
     print(json.dumps(out))
 
