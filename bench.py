@@ -67,6 +67,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_cells(cells_per_rank, rank):
+    """This rank's slice of one seeded stream of cells_per_rank * world cells
+    (weak scaling: every rank integrates its own independent cells)."""
+    return slice(rank * cells_per_rank, (rank + 1) * cells_per_rank)
+
+
+def combine_ranks(units, ms, world, device):
+    """(units summed over ranks, the slowest rank's milliseconds); the whole
+    job's throughput is units / ms.  No collective on the data path: this is
+    the only exchange, after the timed region."""
+    if world == 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    t_max = torch.tensor([ms], dtype=torch.float64, device=device)
+    s_sum = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s_sum, op=dist.ReduceOp.SUM)
+    return float(s_sum.item()), float(t_max.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -377,7 +398,7 @@ def main():
     t_end = a.t_end_yr * YEAR
     # every rank takes its own slice of one seeded stream of cells
     d, T, nH, Av, y0 = make(WORKLOAD, cells=C * world)
-    sl = slice(rank * C, (rank + 1) * C)
+    sl = rank_cells(C, rank)
     T, nH, Av, y0 = T[sl], nH[sl], Av[sl], np.ascontiguousarray(y0[:, sl])
     net = B.Network(d, local)
     info = net.info()
@@ -428,14 +449,7 @@ def main():
     ms = e0.elapsed_time(e1)
     launches, kern_ms, kern_n = state.timing()
     launches += a.steps       # the state counts its own kernels; add one rates_eval per step
-    tot = torch.tensor([cell_steps, ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        t_max = tot[1:].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        s_sum = tot[:1].clone()
-        dist.all_reduce(s_sum, op=dist.ReduceOp.SUM)
-        cell_steps, ms = float(s_sum.item()), float(t_max.item())
+    cell_steps, ms = combine_ranks(cell_steps, ms, world, dev)
     value = cell_steps / (ms * 1e-3)
 
     # end to end through the public calls with host buffers
@@ -468,14 +482,7 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         e_ms = f0.elapsed_time(f1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_ms, e2e_steps], dtype=torch.float64, device=dev)
-            m = t[:1].clone()
-            dist.all_reduce(m, op=dist.ReduceOp.MAX)
-            s_ = t[1:].clone()
-            dist.all_reduce(s_, op=dist.ReduceOp.SUM)
-            e_ms, e2e_steps = float(m.item()), float(s_.item())
+        e2e_steps, e_ms = combine_ranks(e2e_steps, e_ms, world, dev)
         e2e = {"value": e2e_steps / (e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(C * (3 + d.n_s) * 8),
                "d2h_bytes_per_step": int(d.n_s * ld * 8 + stats.numel())}
