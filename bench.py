@@ -57,6 +57,9 @@ def args_():
     p.add_argument("--rhs-cells", type=int, default=4096,
                    help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
     p.add_argument("--rhs-only", action="store_true", help="run only the format grid and print it")
+    p.add_argument("--no-accuracy", action="store_true", help="skip the per-precision accuracy check")
+    p.add_argument("--accuracy-only", action="store_true",
+                   help="run only the accuracy check and print it with every species")
     return p.parse_args()
 
 
@@ -318,6 +321,55 @@ def measured_peaks():
     return {"hbm_gbs": hbm, "fp64_tflops": 1.19}
 
 
+def accuracy_vs_oracle(B, dev, full=False):
+    """Final abundances of the four stored 470 x 6000 cells (T 10-1000 K, n_H
+    1e2-1e8, A_V 0-20, atomic start, 1e6 yr) in every precision, against the
+    oracle's rtol-1e-10 solution stored in tests/golden (written by
+    make_integrate_truth.py, which calls only the oracle).  Per species: the
+    largest and the median relative error over the cells, for abundances
+    above 1e-20; the oracle's own rtol-1e-6 solution is scored the same way."""
+    import numpy as np
+    import torch
+    from synth import cells as sc
+    from synth import network as sn
+    with open(os.path.join(ROOT, "tests", "golden", "integrate_truth_large.json")) as fh:
+        ref = json.load(fh)
+    truth = np.array(ref["y"]).T
+    n_s, C = truth.shape
+    d = sn.generate(2312, 470, 6000)
+    T, nH, Av = sc.conditions(4998, C, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0))
+    y0 = sc.atomic_start(d, C)
+    net = B.Network(d, dev.index or 0)
+    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
+    live = truth > 1e-20
+
+    def score(y):
+        rel = np.where(live, np.abs(y - truth) / np.where(live, truth, 1.0), np.nan)
+        mx = np.nanmax(np.where(np.isnan(rel), -1.0, rel), axis=1)
+        med = np.array([np.median(r[~np.isnan(r)]) if np.any(~np.isnan(r)) else -1.0 for r in rel])
+        ok = mx >= 0
+        worst = np.argsort(-mx)[:5]
+        out = {"max_rel": float(mx[ok].max()), "median_of_species_medians": float(np.median(med[ok])),
+               "species_scored": int(ok.sum()),
+               "worst": [[d.names[i], float(mx[i])] for i in worst]}
+        if full:
+            out["per_species"] = {d.names[i]: [float(mx[i]), float(med[i])] for i in range(n_s) if ok[i]}
+        return out
+
+    res = {"cells": C, "reference": "oracle BDF at rtol 1e-10 (tests/golden/integrate_truth_large.json)",
+           "oracle_rtol6": score(np.array(ref["y_rtol6"]).T)}
+    for prec in ("fp64", "mixed", "tf32"):
+        st = B.State(net, C, precision=prec)
+        yd = y0d.clone()
+        code = st.integrate(kd, yd, 1e6 * YEAR, C)
+        torch.cuda.synchronize()
+        res[prec] = score(yd.cpu().numpy()[:, :C])
+        res[prec]["status"] = int(code)
+        st.close()
+    net.close()
+    return res
+
+
 def adjoint_measurement(B, C, dev):
     """Discrete adjoint on the adjoint workload (470 x 6000, 1e5 yr, FP64,
     checkpoints every 16 steps): one recorded forward integrate and one reverse
@@ -390,6 +442,10 @@ def main():
     if a.rhs_only:
         if rank == 0:
             print(json.dumps(rhs_jac_grid(B, a.rhs_cells, dev, measured_peaks())))
+        return
+    if a.accuracy_only:
+        if rank == 0:
+            print(json.dumps(accuracy_vs_oracle(B, dev, full=True)))
         return
     if world > 1:
         import torch.distributed as dist
@@ -521,6 +577,7 @@ def main():
     del state
     adj = adjoint_measurement(B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = rhs_jac_grid(B, a.rhs_cells, dev, measured_peaks()) if a.rhs_cells > 0 else None
+    acc = None if a.no_accuracy else accuracy_vs_oracle(B, dev)
     cpu = None
     if not a.no_cpu:
         n = a.cpu_cells or host_cores()
@@ -543,7 +600,7 @@ def main():
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64": fp64, "adjoint": adj, "rhs_jac": rhs,
+        "fp64": fp64, "adjoint": adj, "rhs_jac": rhs, "accuracy": acc,
     }
     print(json.dumps(out))
 
