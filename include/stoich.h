@@ -123,6 +123,27 @@ sm_status sm_net_set_format(sm_net* net, int32_t fmt, int32_t order, int32_t sel
                             int32_t sell_sigma);
 sm_status sm_net_get_info(const sm_net* net, sm_net_info* info);
 
+/* Result of sm_net_autotune. */
+typedef struct {
+    int32_t fmt, order, sell_C, sell_sigma;  /* the selected traversal          */
+    double us;                               /* its median sm_rhs_eval time     */
+    int32_t candidates;                      /* traversals timed (0 if cached)  */
+    int32_t cached;                          /* 1: taken from the process cache */
+} sm_tune_result;
+
+/* Measured choice of the sm_rhs_eval traversal (the paper's storage-format
+ * comparison, Section 3, done per network and GPU): builds each candidate of
+ * a fixed grid (CRS, COO, CCS x row orders; SELL-C-sigma with C in {4, 8, 32}
+ * and sigma in {1, 8C, n_s}), runs sm_rhs_eval on the caller's device arrays
+ * d_k = k'[n_r][ld], d_y = x[n_s][ld] (C cells) writing d_f = f[n_s][ld], times
+ * one warm-up and five calls with CUDA events on `stream` (median), and leaves
+ * the fastest selected (as sm_net_set_format would).  The choice is cached for
+ * the process per (network content, device name, C rounded up to a power of
+ * two); force = 1 measures again.  Synchronises with `stream`.  SM_EINVAL on
+ * bad arguments or a host-only network. */
+sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, const double* d_y, double* d_f,
+                          int64_t ld, int32_t force, void* stream, sm_tune_result* out);
+
 /* Export host copies of internal structures for bit-exact checks.  what:
  *  SM_X_ROW_ORDER int32[n_s]    rows (species) in traversal order
  *  SM_X_COL_ORDER int32[n_r]    columns (reactions) in traversal order

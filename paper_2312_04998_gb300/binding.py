@@ -47,6 +47,11 @@ class NetInfo_c(ct.Structure):
                 ("rhs_flops", ct.c_double), ("jac_bytes", ct.c_double), ("jac_flops", ct.c_double)]
 
 
+class TuneResult_c(ct.Structure):
+    _fields_ = [("fmt", ct.c_int32), ("order", ct.c_int32), ("sell_C", ct.c_int32), ("sell_sigma", ct.c_int32),
+                ("us", ct.c_double), ("candidates", ct.c_int32), ("cached", ct.c_int32)]
+
+
 class Opts_c(ct.Structure):
     _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("gamma_tol", ct.c_double),
                 ("newton_tol", ct.c_double), ("eta_max", ct.c_double), ("eta_keep", ct.c_double),
@@ -73,6 +78,8 @@ _SIGS = [
     ("sm_net_free", ct.c_int32, [ct.c_void_p]),
     ("sm_net_set_format", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]),
     ("sm_net_get_info", ct.c_int32, [ct.c_void_p, ct.POINTER(NetInfo_c)]),
+    ("sm_net_autotune", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                     ct.c_int64, ct.c_int32, ct.c_void_p, ct.POINTER(TuneResult_c)]),
     ("sm_net_export_size", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_size_t)]),
     ("sm_net_export", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_size_t]),
     ("sm_rates_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
@@ -219,6 +226,17 @@ class Network:
         _check(lib().sm_rates_eval(self.h, int(C), _dptr(T), _dptr(nH), _dptr(Av), float(zeta),
                                    _dptr(k), int(self._ld(k)), _stream(k.device)), "sm_rates_eval")
         return k
+
+    def autotune(self, k, y, f, C, force=False):
+        """Times sm_rhs_eval over the candidate traversals on these device
+        arrays and leaves the fastest selected; returns the choice as a dict."""
+        r = TuneResult_c()
+        _check(lib().sm_net_autotune(self.h, int(C), _dptr(k), _dptr(y), _dptr(f), int(self._ld(k, y, f)),
+                                     int(bool(force)), _stream(y.device), ct.byref(r)), "sm_net_autotune")
+        inv_f = {v: k_ for k_, v in FMT.items()}
+        inv_o = {v: k_ for k_, v in ORDER.items()}
+        return {"fmt": inv_f[r.fmt], "order": inv_o[r.order], "sell_C": r.sell_C, "sell_sigma": r.sell_sigma,
+                "us": r.us, "candidates": r.candidates, "cached": bool(r.cached)}
 
     def rhs_eval(self, k, y, f, C):
         ld = self._ld(k, y, f)

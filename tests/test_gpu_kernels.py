@@ -202,3 +202,31 @@ def test_full_size_sampled(torch, B, fmt):
         ref = S @ ok.reaction_rates(d, k[:, c], y[:, c])
         scale = np.abs(S) @ np.abs(ok.reaction_rates(d, k[:, c], y[:, c]))
         assert np.all(np.abs(f[:, c] - ref) <= RTOL_F * scale + 1e-300)
+
+
+def test_autotune_selects_a_measured_format_and_keeps_parity(torch, B):
+    """sm_net_autotune times the candidate traversals, leaves the fastest
+    selected (reported by sm_net_get_info), caches it per network / device /
+    batch size, and rhs_eval keeps the usual 1e-12 bar afterwards."""
+    d = sn.generate(2312, 470, 6000)
+    C = 512
+    ld = B.pad_ld(C)
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e7), (0.0, 10.0))
+    y = sc.loguniform_abundances(d, 4998, C)
+    k = ok.rate_coefficients(d, T, nH, Av)
+    net = B.Network(d, 0)
+    kd, yd = dev_mat(torch, k, ld, 0.0), dev_mat(torch, y, ld, 0.0)
+    fd = torch.zeros((d.n_s, ld), dtype=torch.float64, device="cuda")
+    r = net.autotune(kd, yd, fd, C)
+    assert not r["cached"] and r["candidates"] >= 10 and r["us"] > 0
+    info = net.info()
+    assert (info["fmt"], info["order"]) == (B.FMT[r["fmt"]], B.ORDER[r["order"]])
+    assert (info["sell_C"], info["sell_sigma"]) == (r["sell_C"], r["sell_sigma"])
+    net.set_format("crs", "none", 1, 1)
+    r2 = net.autotune(kd, yd, fd, C - 100)          # same power-of-two bucket: cached
+    assert r2["cached"] and (r2["fmt"], r2["order"], r2["sell_C"]) == (r["fmt"], r["order"], r["sell_C"])
+    assert net.info()["fmt"] == B.FMT[r["fmt"]]
+    net.rhs_eval(kd, yd, fd, C)
+    net.sync()
+    f = fd.cpu().numpy()[:, :C]
+    assert np.all(np.abs(f - ok.rhs(d, k, y)) <= RTOL_F * ok.rhs_scale(d, k, y) + 1e-300)

@@ -165,3 +165,13 @@ def test_device_calls_rejected_on_host_only_network(B):
     assert L.sm_net_set_format(net.h, 9, 0, 1, 1) == B.SM_EINVAL
     assert L.sm_net_export(net.h, 99, None, 0) == B.SM_EINVAL
     del ct
+
+
+def test_autotune_needs_a_device_network(B):
+    """sm_net_autotune times kernels: a host-only network is refused."""
+    import ctypes as ct
+    d = sn.generate(2312, 32, 180)
+    net = B.Network(d, device=-1)
+    r = B.TuneResult_c()
+    code = B.lib().sm_net_autotune(net.h, 32, None, None, None, 32, 0, None, ct.byref(r))
+    assert code == B.SM_EINVAL
