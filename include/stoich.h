@@ -114,6 +114,25 @@ typedef struct {
 sm_status sm_net_build(const sm_net_desc* d, int32_t device, sm_net** out);
 sm_status sm_net_free(sm_net* net);
 
+/* Seeded synthetic network of the paper's shape (the UMIST network of Section
+ * 3 is not distributed): species from H, C, O and e- (neutral, cationic and
+ * small anionic compositions, small first, alphabetical by formula), reactions
+ * grouped by class 60 % two-body, 20 % cosmic ray, 15 % photo, 5 % dissociative
+ * recombination, each with 1-2 reactants and 1-4 products conserving every
+ * element and the charge; two-body / DR log10 alpha ~ U[-12,-9], beta ~
+ * U[-1,1], gamma ~ U[0,500] K; cosmic ray log10 alpha ~ U[0,3]; photo log10
+ * alpha ~ U[-11,-9], gamma ~ U[1,3].  Every draw comes from counter-based
+ * SplitMix64 streams of `seed`, so the arrays are identical on every platform.
+ * sm_synth_network fills caller-owned host arrays in the layout of
+ * sm_net_desc (comp [n_s][4], reactants [n_r][2], products [n_r][4] padded with
+ * -1, rclass, alpha, beta, gamma [n_r]); sm_net_build_synthetic builds the
+ * network from them (as sm_net_build with n_elem = 3).  SM_EINVAL if n_s < 12,
+ * n_r < 1, an array is NULL, or the species set cannot hold n_r distinct
+ * reactions. */
+sm_status sm_synth_network(uint64_t seed, int32_t n_s, int32_t n_r, int32_t* comp, int32_t* reactants,
+                           int32_t* products, int8_t* rclass, double* alpha, double* beta, double* gamma);
+sm_status sm_net_build_synthetic(uint64_t seed, int32_t n_s, int32_t n_r, int32_t device, sm_net** out);
+
 /* Select the traversal used by sm_rhs_eval: fmt (SM_FMT_*), row order
  * (SM_ORDER_*; nnz = descending nonzero count, stable, Section 3; RCM =
  * reverse Cuthill-McKee on pattern(S S^T)), and for SELL the slice height C

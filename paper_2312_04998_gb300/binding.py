@@ -76,6 +76,10 @@ _SIGS = [
     ("sm_status_str", ct.c_char_p, [ct.c_int32]),
     ("sm_net_build", ct.c_int32, [ct.POINTER(NetDesc_c), ct.c_int32, ct.POINTER(ct.c_void_p)]),
     ("sm_net_free", ct.c_int32, [ct.c_void_p]),
+    ("sm_synth_network", ct.c_int32, [ct.c_uint64, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                      ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    ("sm_net_build_synthetic", ct.c_int32, [ct.c_uint64, ct.c_int32, ct.c_int32, ct.c_int32,
+                                            ct.POINTER(ct.c_void_p)]),
     ("sm_net_set_format", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]),
     ("sm_net_get_info", ct.c_int32, [ct.c_void_p, ct.POINTER(NetInfo_c)]),
     ("sm_net_autotune", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
@@ -184,6 +188,16 @@ class Network:
         self.device = device
         self.n_s, self.n_r = n_s, n_r
 
+    @classmethod
+    def synthetic(cls, seed: int, n_s: int, n_r: int, device: int = 0):
+        """A network drawn and built inside the library (sm_net_build_synthetic)."""
+        self = cls.__new__(cls)
+        h = ct.c_void_p()
+        _check(lib().sm_net_build_synthetic(int(seed), int(n_s), int(n_r), int(device), ct.byref(h)),
+               "sm_net_build_synthetic")
+        self.h, self.device, self.n_s, self.n_r, self._keep = h, device, n_s, n_r, {}
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             lib().sm_net_free(self.h)
@@ -260,6 +274,20 @@ class Network:
     def sync(self):
         import torch
         _check(lib().sm_sync(self.h, _stream(torch.device("cuda", self.device))), "sm_sync")
+
+
+def synth_network(seed: int, n_s: int, n_r: int) -> dict:
+    """The library's seeded synthetic network arrays (sm_synth_network)."""
+    comp = np.zeros((n_s, 4), dtype=np.int32)
+    reac = np.zeros((n_r, 2), dtype=np.int32)
+    prod = np.zeros((n_r, 4), dtype=np.int32)
+    cls = np.zeros(n_r, dtype=np.int8)
+    alpha, beta, gamma = np.zeros(n_r), np.zeros(n_r), np.zeros(n_r)
+    _check(lib().sm_synth_network(int(seed), int(n_s), int(n_r), comp.ctypes.data, reac.ctypes.data,
+                                  prod.ctypes.data, cls.ctypes.data, alpha.ctypes.data, beta.ctypes.data,
+                                  gamma.ctypes.data), "sm_synth_network")
+    return {"comp": comp, "reactants": reac, "products": prod, "rclass": cls, "alpha": alpha, "beta": beta,
+            "gamma": gamma}
 
 
 def default_opts(**kw) -> Opts_c:

@@ -175,3 +175,31 @@ def test_autotune_needs_a_device_network(B):
     r = B.TuneResult_c()
     code = B.lib().sm_net_autotune(net.h, 32, None, None, None, 32, 0, None, ct.byref(r))
     assert code == B.SM_EINVAL
+
+
+@pytest.mark.parametrize("seed,n_s,n_r", [(2312, 32, 180), (2312, 470, 6000), (99, 64, 700)])
+def test_library_synthetic_network_equals_input_generator(B, seed, n_s, n_r):
+    """sm_synth_network draws the same arrays, bit for bit, as the package's
+    Python input generator for the same seed (both are integer decisions on
+    the same SplitMix64 streams)."""
+    a = B.synth_network(seed, n_s, n_r)
+    d = sn.generate(seed, n_s, n_r)
+    for key, ref in (("comp", d.comp), ("reactants", d.reactants), ("products", d.products),
+                     ("rclass", d.rclass), ("alpha", d.alpha), ("beta", d.beta), ("gamma", d.gamma)):
+        assert np.array_equal(a[key], ref), key
+
+
+def test_build_synthetic_matches_build_from_arrays(B):
+    d = sn.generate(2312, 470, 6000)
+    n1 = B.Network(d, device=-1)
+    n2 = B.Network.synthetic(2312, 470, 6000, device=-1)
+    assert n1.info() == n2.info()
+    for what in (B.X_FMT_PTR, B.X_FMT_IDX, B.X_JPAT_PTR, B.X_JPAT_COL, B.X_LU_PERM):
+        assert np.array_equal(n1.export(what), n2.export(what))
+
+
+def test_synthetic_network_rejects_bad_sizes(B):
+    import ctypes as ct
+    h = ct.c_void_p()
+    assert B.lib().sm_net_build_synthetic(1, 8, 100, -1, ct.byref(h)) == B.SM_EINVAL
+    assert B.lib().sm_net_build_synthetic(1, 32, 0, -1, ct.byref(h)) == B.SM_EINVAL
