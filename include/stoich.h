@@ -327,6 +327,22 @@ sm_status sm_step_bdf(sm_state* st, const double* d_k, int64_t ld, int32_t attem
 sm_status sm_state_read(sm_state* st, double* d_y, int64_t ld, sm_cell_stats* d_stats,
                         int64_t* h_running, void* stream);
 
+/* Checkpoint / resume of an integration.  sm_state_save writes an image of
+ * the state (per-cell time, step size, order, counters and status, the step
+ * history and working vectors, the step records, and with with_factors = 1
+ * the factorised Newton matrices) into the caller's host buffer; *needed
+ * receives the image size (call with host = NULL to query it; the factors are
+ * n_s x ldm values per cell of capacity, FP32 or FP64).  sm_state_load puts an
+ * image back into a state created for the same network size, capacity,
+ * precision and record length (SM_EINVAL otherwise); stepping it then
+ * continues the saved integration with the loading state's options.  With the
+ * factors the continuation is bit-identical to an uninterrupted run; without
+ * them every cell refactorises its Newton matrix on its next attempt.  Both
+ * synchronise with the state's stream before returning. */
+sm_status sm_state_save(sm_state* st, int32_t with_factors, void* host, size_t bytes, size_t* needed,
+                        void* stream);
+sm_status sm_state_load(sm_state* st, const void* host, size_t bytes, void* stream);
+
 /* Instrumentation: *launches = kernels the state has launched so far, and,
  * when opts.timing_kind selects a class, *ms = summed CUDA-event durations of
  * that class's launches (*timed = how many were timed; the RHS class times

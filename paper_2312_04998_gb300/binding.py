@@ -109,6 +109,9 @@ _SIGS = [
     ("sm_step_bdf", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p]),
     ("sm_state_read", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p,
                                    ct.POINTER(ct.c_int64), ct.c_void_p]),
+    ("sm_state_save", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_size_t, ct.POINTER(ct.c_size_t),
+                                   ct.c_void_p]),
+    ("sm_state_load", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     ("sm_state_steps", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                     ct.c_int64, ct.c_void_p]),
     ("sm_adjoint", ct.c_int32, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int32,
@@ -374,6 +377,23 @@ class State:
                                    _stream(dev)), "sm_state_read")
         return running.value
 
+
+    def save(self, with_factors=True):
+        """Host image of the state (numpy uint8 array), see sm_state_save."""
+        import torch
+        n = ct.c_size_t()
+        _check(lib().sm_state_save(self.h, int(bool(with_factors)), None, 0, ct.byref(n), None), "sm_state_save")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().sm_state_save(self.h, int(bool(with_factors)), buf.ctypes.data, buf.nbytes, ct.byref(n),
+                                   _stream(torch.device("cuda", self.net.device))), "sm_state_save")
+        return buf
+
+    def load(self, image):
+        import torch
+        image = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(lib().sm_state_load(self.h, image.ctypes.data, image.nbytes,
+                                   _stream(torch.device("cuda", self.net.device))), "sm_state_load")
+        self.generation += 1
 
     def steps_log(self, m_max, C=None):
         """Recorded accepted steps: device tensors t, h (float64) and q (int32),

@@ -18,6 +18,7 @@
 // reads back only the number of running cells between groups.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -1256,6 +1257,14 @@ __global__ void read_kernel(Dev d, double* __restrict__ yout, int64_t ldu, sm_ce
   }
 }
 
+// After a state is loaded without its Newton factors: every cell refreshes
+// its Newton matrix on its next attempt.
+__global__ void need_j_kernel(Dev d) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  d.flags[c] |= F_NEED_J;
+}
+
 // counters[1] = cells still running, counters[2] = cells stopped short of t_end
 __global__ void count_running_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2444,6 +2453,127 @@ sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, in
 }
 
 }  // extern "C"
+
+namespace {
+
+// Image of a state: this header, then the raw bytes of the per-cell scalars,
+// the history and working vectors, the step records, and (optionally) the
+// Newton factors, in that order.
+struct StateImage {
+  uint64_t magic;
+  int32_t version, n_s, n_r, precision;
+  int64_t cap, ld, C, lu_stride;
+  double t_end;
+  int32_t record, with_factors;
+  uint64_t bytes[5];   // scal_d, scal_i, vec, rec_d + rec_i, lu
+};
+constexpr uint64_t kImageMagic = 0x534D5354415445ull;   // "SMSTATE"
+
+void image_sizes(const sm_state* st, int with_factors, uint64_t* b) {
+  b[0] = st->scal_d.bytes;
+  b[1] = st->scal_i.bytes;
+  b[2] = st->vec.bytes;
+  b[3] = st->rec_d.bytes + st->rec_i.bytes;
+  b[4] = with_factors ? st->lu.bytes : 0;
+}
+
+}  // namespace
+
+extern "C" sm_status sm_state_save(sm_state* st, int32_t with_factors, void* host, size_t bytes,
+                                   size_t* needed, void* stream) {
+  if (!st || !needed) return SM_EINVAL;
+  uint64_t b[5];
+  image_sizes(st, with_factors, b);
+  const size_t total = sizeof(StateImage) + b[0] + b[1] + b[2] + b[3] + b[4];
+  *needed = total;
+  if (!host) return SM_OK;
+  if (bytes < total || st->C < 1) return SM_EINVAL;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  StateImage im{};
+  im.magic = kImageMagic;
+  im.version = 1;
+  im.n_s = st->d.n;
+  im.n_r = st->d.n_r;
+  im.precision = st->opts.precision;
+  im.cap = st->cap;
+  im.ld = st->ld;
+  im.C = st->C;
+  im.lu_stride = st->d.lu_stride;
+  im.t_end = st->t_end;
+  im.record = st->d.record;
+  im.with_factors = with_factors ? 1 : 0;
+  for (int i = 0; i < 5; ++i) im.bytes[i] = b[i];
+  std::memcpy(host, &im, sizeof im);
+  char* dst = static_cast<char*>(host) + sizeof im;
+  const DevArray* parts[3] = {&st->scal_d, &st->scal_i, &st->vec};
+  for (int i = 0; i < 3; ++i) {
+    SM_TRY_CUDA(cudaMemcpyAsync(dst, parts[i]->p, parts[i]->bytes, cudaMemcpyDeviceToHost, st->s));
+    dst += parts[i]->bytes;
+  }
+  if (st->rec_d.bytes) {
+    SM_TRY_CUDA(cudaMemcpyAsync(dst, st->rec_d.p, st->rec_d.bytes, cudaMemcpyDeviceToHost, st->s));
+    dst += st->rec_d.bytes;
+  }
+  if (st->rec_i.bytes) {
+    SM_TRY_CUDA(cudaMemcpyAsync(dst, st->rec_i.p, st->rec_i.bytes, cudaMemcpyDeviceToHost, st->s));
+    dst += st->rec_i.bytes;
+  }
+  if (b[4]) SM_TRY_CUDA(cudaMemcpyAsync(dst, st->lu.p, b[4], cudaMemcpyDeviceToHost, st->s));
+  SM_TRY_CUDA(cudaStreamSynchronize(st->s));
+  return join_out(st, stream);
+}
+
+extern "C" sm_status sm_state_load(sm_state* st, const void* host, size_t bytes, void* stream) {
+  if (!st || !host || bytes < sizeof(StateImage)) return SM_EINVAL;
+  StateImage im;
+  std::memcpy(&im, host, sizeof im);
+  uint64_t b[5];
+  image_sizes(st, im.with_factors, b);
+  const size_t total = sizeof(StateImage) + b[0] + b[1] + b[2] + b[3] + b[4];
+  // the image must come from a state of the same shape: network size,
+  // capacity, precision and recording
+  if (im.magic != kImageMagic || im.version != 1 || im.n_s != st->d.n || im.n_r != st->d.n_r ||
+      im.precision != st->opts.precision || im.cap != st->cap || im.ld != st->ld ||
+      im.lu_stride != st->d.lu_stride || im.record != st->d.record || im.C < 1 || im.C > st->cap ||
+      bytes < total)
+    return SM_EINVAL;
+  for (int i = 0; i < 5; ++i)
+    if (im.bytes[i] != b[i]) return SM_EINVAL;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  const char* src = static_cast<const char*>(host) + sizeof im;
+  const DevArray* parts[3] = {&st->scal_d, &st->scal_i, &st->vec};
+  for (int i = 0; i < 3; ++i) {
+    SM_TRY_CUDA(cudaMemcpyAsync(parts[i]->p, src, parts[i]->bytes, cudaMemcpyHostToDevice, st->s));
+    src += parts[i]->bytes;
+  }
+  if (st->rec_d.bytes) {
+    SM_TRY_CUDA(cudaMemcpyAsync(st->rec_d.p, src, st->rec_d.bytes, cudaMemcpyHostToDevice, st->s));
+    src += st->rec_d.bytes;
+  }
+  if (st->rec_i.bytes) {
+    SM_TRY_CUDA(cudaMemcpyAsync(st->rec_i.p, src, st->rec_i.bytes, cudaMemcpyHostToDevice, st->s));
+    src += st->rec_i.bytes;
+  }
+  if (b[4]) SM_TRY_CUDA(cudaMemcpyAsync(st->lu.p, src, b[4], cudaMemcpyHostToDevice, st->s));
+  st->C = im.C;
+  st->t_end = im.t_end;
+  st->d.C = im.C;
+  st->d.t_end = im.t_end;
+  if (!im.with_factors) {
+    need_j_kernel<<<blocks(im.C, 128), 128, 0, st->s>>>(st->d);
+    SM_TRY_CUDA(cudaGetLastError());
+    st->launches += 1;
+  }
+  // the host copies must be complete before the caller may free its buffer
+  SM_TRY_CUDA(cudaStreamSynchronize(st->s));
+  return join_out(st, stream);
+}
 
 extern "C" sm_status sm_state_timing(const sm_state* st, int64_t* launches, double* ms, int64_t* timed) {
   if (!st) return SM_EINVAL;

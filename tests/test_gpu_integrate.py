@@ -280,3 +280,52 @@ def test_split_newton_rounds_are_bit_identical(torch, B, precision):
         out.append((y, stats["steps"].copy(), stats["newton_iters"].copy()))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("with_factors", [True, False])
+def test_state_save_load_resume(torch, B, with_factors):
+    """Stop an integration after 40 attempts, save the state to host memory,
+    load it into a new state and finish there: with the Newton factors saved
+    the result is the same bits as an uninterrupted run; without them (every
+    cell refactorises once on resume) it is another rtol-1e-6 solution of the
+    same problem, a few tolerance units away."""
+    d = sn.generate(2312, 32, 180)
+    C = 40
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
+    k = ok.rate_coefficients(d, T, nH, Av)
+    y0 = sc.atomic_start(d, C)
+    t_end = 1e3 * YEAR
+    y_ref, s_ref, code = run_gpu(torch, B, d, k, y0, t_end)
+    assert code == B.SM_OK
+    ld = B.pad_ld(C)
+    net = B.Network(d, 0)
+    kd = dev(torch, k, ld)
+    a = B.State(net, C)
+    a.init(kd, dev(torch, y0, ld), t_end, C)
+    a.step(kd, 40)
+    assert a.read() > 0                       # interrupted mid-run
+    image = a.save(with_factors)
+    del a
+    b = B.State(net, C)
+    b.load(image)
+    for _ in range(2000):
+        b.step(kd, 8)
+        if b.read() == 0:
+            break
+    y = torch.zeros((d.n_s, ld), dtype=torch.float64, device="cuda")
+    stats = B.stats_tensor(C, "cuda")
+    assert b.read(y, stats) == 0
+    torch.cuda.synchronize()
+    y, s = y.cpu().numpy()[:, :C], B.stats_to_numpy(stats)
+    assert np.all(s["status"] == B.CELL_OK) and np.all(s["t"] == t_end)
+    if with_factors:
+        assert np.array_equal(y, y_ref)
+        for key in ("steps", "rejects", "newton_iters", "jac_evals"):
+            assert np.array_equal(s[key], s_ref[key]), key
+    else:
+        units = np.abs(y - y_ref) / (1e-6 * np.abs(y_ref) + 1e-20)
+        assert units.max() <= 100.0, units.max()
+    # an image does not fit a state of another shape
+    c = B.State(net, C + 64)
+    with pytest.raises(B.StoichError):
+        c.load(image)
