@@ -15,7 +15,10 @@
 //             substitution and the WRMS convergence test;
 //   finish    thread per cell: error test, order / step selection, history.
 // The host enqueues attempts in groups (captured once in a CUDA graph) and
-// reads back only the number of running cells between groups.
+// reads back only the number of running cells between groups.  The same file
+// holds the step recording and the discrete adjoint of the frozen-step map
+// (sm_state_steps, sm_adjoint, sm_replay) and checkpoint / resume
+// (sm_state_save, sm_state_load).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
