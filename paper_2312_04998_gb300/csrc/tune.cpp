@@ -130,6 +130,7 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
       sm_status st = net_select_format(net, r.fmt, r.order, r.sell_C, r.sell_sigma);
       if (st != SM_OK) return st;
       r.cached = 1;
+      r.candidates = 0;   // nothing was timed by this call
       *out = r;
       return SM_OK;
     }

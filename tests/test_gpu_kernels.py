@@ -224,7 +224,8 @@ def test_autotune_selects_a_measured_format_and_keeps_parity(torch, B):
     assert (info["sell_C"], info["sell_sigma"]) == (r["sell_C"], r["sell_sigma"])
     net.set_format("crs", "none", 1, 1)
     r2 = net.autotune(kd, yd, fd, C - 100)          # same power-of-two bucket: cached
-    assert r2["cached"] and (r2["fmt"], r2["order"], r2["sell_C"]) == (r["fmt"], r["order"], r["sell_C"])
+    assert r2["cached"] and r2["candidates"] == 0
+    assert (r2["fmt"], r2["order"], r2["sell_C"]) == (r["fmt"], r["order"], r["sell_C"])
     assert net.info()["fmt"] == B.FMT[r["fmt"]]
     net.rhs_eval(kd, yd, fd, C)
     net.sync()
