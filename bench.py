@@ -1,13 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the batched stiff-chemistry integrator.
 
-Workload (one step): the seeded synthetic network of 470 species x 6000
-reactions, 65,536 independent cells of uneven stiffness (T 10-1000 K, n_H
-1e2-1e8 cm^-3, A_V 0-20, atomic start), rate coefficients evaluated on the
-GPU and every cell integrated to 1e6 yr with the library's BDF/Newton method
-at rtol 1e-6 / atol 1e-20.  Metric: accepted cell-steps per second.
+Headline workload: the seeded synthetic network of 470 species x 6000
+reactions and 65,536 independent cells of uneven stiffness (T 10-1000 K, n_H
+1e2-1e8 cm^-3, A_V 0-20, atomic start), every cell integrated to 1e6 yr with
+the library's BDF/Newton method at rtol 1e-6 / atol 1e-20 in the batched
+mixed-precision mode.  Metric: accepted cell-steps per second.
 
-    python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
+One bench step is one slice of a single integration of the whole batch: the
+first step evaluates the rate coefficients (sm_rates_eval) and starts every
+cell at t = 0 (sm_state_init); every step runs a fixed number of BDF attempts
+for all unfinished cells (sm_step_bdf); the last step continues until every
+cell has reached t_end.  The K timed steps therefore cover exactly one
+complete integration; cell-steps are that integration's accepted steps.  The
+warm-up runs W slices of a separate integration of the same batch (graph
+capture and clocks) and is discarded.
+
+After the headline line's own measurements the same JSON line carries:
+  fp64_vs_mixed   16,384 cells integrated in the plain FP64 mode and in the
+                  mixed mode, with the per-species error of both against the
+                  oracle's rtol-1e-10 solution on 32 stiffness-stratified cells
+  adjoint         1024 cells to 1e5 yr in FP64: reverse sweep for 8 targets
+                  against one recorded forward integrate
+  rhs_jac         rhs_eval per storage format / row order and jac_eval on
+                  4096 cells, against the FP64-pipe ceiling
+  cpu_baseline    the oracle on the host cores: 64 stratified cells, each
+                  integrated over the whole interval
+
+    python bench.py [--gpus N --steps K --warmup W] [--precision mixed|tf32|fp64]
     python bench.py --impl reference ...      # the CPU oracle on a sample
 
 Multi-GPU (torchrun): every rank integrates its own 65,536 cells (weak
@@ -28,38 +48,55 @@ sys.path.insert(0, ROOT)
 
 YEAR = 3.15576e7
 WORKLOAD = "integrate_470x6000_c65536"
+MIXED_WORKLOAD = "mixed_470x6000_c16384"
 METRIC = "cell-steps/s (470 sp, 6k rx) plain FP64 vs batched mixed; adjoint/forward ratio"
 UNIT = "cell-steps/s"
+STRAT_FILE = os.path.join(ROOT, "tests", "golden", "integrate_truth_strat.json")
+CPU_CELLS = 64
+# every attempt accepts a step, shrinks h or counts a failure, and each cell
+# stops after max_steps (100,000) accepted steps: the last bench step never
+# needs this many attempts unless something is broken
+MAX_TAIL_ATTEMPTS = 2_000_000
 
-# DRAM traffic per refresh-kernel launch unit from the committed ncu capture
-# (profiles/), valid only while the kernel source is unchanged.
+# Peaks of the pipes that bind these kernels, from unit counts and the
+# 2.07 GHz maximum SM clock of this GPU (152 SMs): FP32 128 lanes x 2 flops,
+# FP64 4 flops per SM per clock.  HBM: the measured copy bandwidth.
+SM_COUNT, SM_GHZ = 152, 2.07
+PEAK_FP32 = SM_COUNT * 128 * 2 * SM_GHZ / 1e3     # TFLOP/s
+PEAK_FP64 = SM_COUNT * 4 * SM_GHZ / 1e3           # TFLOP/s
+
+# DRAM bytes (read + write) per processed unit of a kernel, from a committed
+# ncu capture in profiles/ (named there), keyed on the kernel class, the
+# precision and the hash of integrate.cu at capture time: a changed kernel
+# reports traffic null until it is captured again.
 TRAFFIC = {}
 
 
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "tf32", "fp64"])
     p.add_argument("--cells", type=int, default=65536)
     p.add_argument("--t-end-yr", type=float, default=1e6)
+    p.add_argument("--attempts-est", type=int, default=1600,
+                   help="expected attempts of one integration; slices are attempts-est / steps long")
     p.add_argument("--time-kernel", default="refresh",
                    choices=["refresh", "rhs", "solve", "predict", "finish"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-cells", type=int, default=0, help="oracle sample size (0 = host cores)")
-    p.add_argument("--fp64-cells", type=int, default=4096,
-                   help="cells of the plain FP64 comparison integrate (0 = skip)")
+    p.add_argument("--mixed-cells", type=int, default=16384,
+                   help="cells of the FP64 vs mixed comparison (0 = skip)")
     p.add_argument("--adjoint-cells", type=int, default=1024,
                    help="cells of the adjoint/forward measurement (0 = skip)")
     p.add_argument("--rhs-cells", type=int, default=4096,
                    help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
-    p.add_argument("--rhs-only", action="store_true", help="run only the format grid and print it")
-    p.add_argument("--no-accuracy", action="store_true", help="skip the per-precision accuracy check")
-    p.add_argument("--accuracy-only", action="store_true",
-                   help="run only the accuracy check and print it with every species")
+    p.add_argument("--budget-s", type=float, default=1200.0,
+                   help="auxiliary measurements start only while the run is younger than this")
+    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe"],
+                   help="run one auxiliary measurement alone and print it")
     return p.parse_args()
 
 
@@ -98,64 +135,143 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def slice_attempts(attempts_est, steps, per=8):
+    """Attempts per bench step: attempts_est / steps rounded up to a whole
+    number of captured attempt groups (`per` attempts each)."""
+    a = -(-max(attempts_est, 1) // max(steps, 1))
+    return -(-a // per) * per
+
+
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# CPU oracle on a stratified sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-CPU_STEPS = 40   # accepted steps per sampled cell (bounds the oracle's CPU time)
+def stratified_cells(n=CPU_CELLS):
+    """n cells of the headline workload at evenly spaced quantiles of the
+    oracle's own step count (rtol 1e-6), taken from the 128 candidates
+    (every 128th of the first 16,384 cells) whose counts
+    tests/golden/integrate_truth_strat.json stores; cells are independent
+    draws of one seeded stream, so these represent all 65,536."""
+    with open(STRAT_FILE) as fh:
+        s = json.load(fh)
+    steps = s["candidate_steps_rtol6"]
+    stride = s["pool_cells"] // len(steps)
+    order = sorted(range(len(steps)), key=lambda i: (steps[i], i))
+    pick = [order[int((i + 0.5) * len(order) / n)] for i in range(n)]
+    return [i * stride for i in pick], [steps[i] for i in pick]
+
+
+_ORACLE_NET = None
 
 
 def _oracle_cell(args):
-    """One sampled cell: returns (accepted steps, seconds spent integrating)."""
-    c, t_end, max_steps = args
+    """One sampled cell integrated by the oracle over the whole interval:
+    returns (accepted steps, seconds spent integrating)."""
+    global _ORACLE_NET
+    c, t_end = args
     from oracle import bdf as ob
     from oracle import kinetics as ok
-    from synth.workloads import make
-    d, T, nH, Av, y0 = make(WORKLOAD, cells=c + 1)
-    k = ok.rate_coefficients(d, T[c:c + 1], nH[c:c + 1], Av[c:c + 1])[:, 0]
+    from oracle import network as on
+    from synth import cells as sc
+    from synth.workloads import NET_SEED, WORKLOADS
+    from synth.network import generate
+    w = WORKLOADS[WORKLOAD]
+    if _ORACLE_NET is None:
+        d = generate(NET_SEED, w.n_s, w.n_r)
+        _ORACLE_NET = (d, on.stoichiometry(d))
+    d, S = _ORACLE_NET
+    T, nH, Av = sc.conditions(4998, c + 1, w.T, w.nH, w.Av)
+    k = ok.rate_coefficients(d, T[c:], nH[c:], Av[c:])[:, 0]
+    y0 = sc.atomic_start(d, 1)[:, 0]
     t0 = time.time()
-    r = ob.integrate_cell(d, k, y0[:, c], t_end, ob.BDFOptions(max_steps=max_steps))
+    r = ob.integrate_cell(d, k, y0, t_end, ob.BDFOptions(), S)
     return r.steps, time.time() - t0
 
 
-def oracle_sample(n_cells, t_end, offset=0, max_steps=CPU_STEPS):
-    """Integrates cells offset..offset+n_cells-1 of the workload with the
-    oracle (first `max_steps` accepted steps of each, from the atomic start),
-    one single-threaded process per host core; returns (steps, wall seconds,
-    processes)."""
-    import multiprocessing as mp
+def _pool_init():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
-    cores = min(host_cores(), n_cells)
-    t0 = time.time()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.map(_oracle_cell, [(offset + i, t_end, max_steps) for i in range(n_cells)])
-    return sum(r[0] for r in res), time.time() - t0, cores
+
+
+def _warm(_):
+    """Imports the oracle and builds the network in a worker, then lingers
+    briefly so that every worker of the pool takes one of these tasks."""
+    _oracle_cell((0, 1e-9))
+    time.sleep(0.5)
+    return 0
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core (spawned: no state of
+    a CUDA context is inherited)."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        _pool_init()
+        self.cores = host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init)
+
+    def warm(self):
+        self.pool.map(_warm, range(2 * self.cores), chunksize=1)
+
+    def run(self, cells, t_end):
+        """(accepted steps summed, wall seconds) for integrating `cells`."""
+        t0 = time.time()
+        res = self.pool.map(_oracle_cell, [(c, t_end) for c in cells], chunksize=1)
+        return sum(r[0] for r in res), time.time() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(t_end):
+    cells, _ = stratified_cells()
+    pool = OraclePool()
+    try:
+        pool.warm()                                 # process start-up and imports, untimed
+        steps, dt = pool.run(cells, t_end)
+    finally:
+        pool.close()
+    return {"value": steps / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": (f"{len(cells)} cells of {WORKLOAD} stratified by stiffness (evenly spaced quantiles of "
+                       f"the oracle's step count among every 128th of the first 16,384 cells), each integrated "
+                       f"over the whole 1e6 yr at rtol 1e-6, one single-threaded process per core; "
+                       f"{steps} accepted steps in {dt:.1f} s"),
+            "cell_steps": steps, "seconds": dt, "steps_per_cell": steps / len(cells)}
 
 
 def reference_arm(a, rank):
+    """The oracle as the reference arm: each step integrates one core's worth
+    of the 64 stratified cells over the whole interval (the four quarters of
+    the sample in turn)."""
     if rank != 0:
         return
     t_end = a.t_end_yr * YEAR
-    n = a.cpu_cells or host_cores()
-    for _ in range(a.warmup):
-        oracle_sample(n, t_end, 0)
-    tot_steps, tot_s = 0, 0.0
-    cores = 1
-    for s in range(a.steps):
-        st, dt, cores = oracle_sample(n, t_end, (s % 4) * n)
-        tot_steps += st
-        tot_s += dt
+    cells, _ = stratified_cells()
+    pool = OraclePool()
+    n = min(pool.cores, len(cells))
+    groups = [cells[i::len(cells) // n][:n] for i in range(len(cells) // n)]
+    try:
+        for _ in range(a.warmup):
+            pool.warm()                              # start-up only
+        tot_steps, tot_s = 0, 0.0
+        for s in range(a.steps):
+            st, dt = pool.run(groups[s % len(groups)], t_end)
+            tot_steps += st
+            tot_s += dt
+    finally:
+        pool.close()
     v = tot_steps / tot_s
-    sample = (f"{n} cells per step of {WORKLOAD}, first {CPU_STEPS} accepted steps of each from the "
-              f"atomic start, one single-threaded process per cell")
+    sample = (f"{n} cells per step from {len(cells)} cells of {WORKLOAD} stratified by stiffness, each "
+              f"integrated over the whole 1e6 yr at rtol 1e-6, one single-threaded process per core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_s / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "cells_per_step": n,
                                         "t_end_yr": a.t_end_yr, "rtol": 1e-6, "atol": 1e-20},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -216,10 +332,10 @@ def timed(fn, stream):
     return r, e0.elapsed_time(e1)
 
 
-def gpu_inputs(B, net, d, T, nH, Av, y0, dev):
-    """Device k' (evaluated by sm_rates_eval) and y0 for C cells."""
+def device_conditions(B, T, nH, Av, dev):
+    """Padded device copies of the cell conditions (padding: harmless values)."""
     import torch
-    C = y0.shape[1]
+    C = len(T)
     ld = B.pad_ld(C)
 
     def padded(v, fill):
@@ -227,32 +343,91 @@ def gpu_inputs(B, net, d, T, nH, Av, y0, dev):
         out[:C] = torch.tensor(v, dtype=torch.float64, device=dev)
         return out
 
+    return padded(T, 100.0), padded(nH, 1.0), padded(Av, 0.0)
+
+
+def gpu_inputs(B, net, d, T, nH, Av, y0, dev):
+    """Device k' (evaluated by sm_rates_eval) and y0 for C cells."""
+    import torch
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+    Td, nHd, Avd = device_conditions(B, T, nH, Av, dev)
     kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
-    net.rates_eval(padded(T, 100.0), padded(nH, 1.0), padded(Av, 0.0), kd, C)
+    net.rates_eval(Td, nHd, Avd, kd, C)
     y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
     y0d[:, :C] = torch.tensor(y0, dtype=torch.float64, device=dev)
     return kd, y0d
 
 
-def fp64_comparison(B, net, d, T, nH, Av, y0, t_end, dev):
-    """The plain FP64 integrator on the first cells of the same workload
-    (FP64-pipe bound at any batch that fills the GPU, so its cell-steps/s is
-    that of the full batch); one short untimed warm-up."""
-    import torch
-    C = y0.shape[1]
-    st = B.State(net, C, precision="fp64")
-    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
-    stats = B.stats_tensor(C, dev)
+def integrate_timed(B, st, kd, y0d, t_end, C, stats, stream):
+    """One whole integration through sm_integrate after an untimed 8-attempt
+    start (graph capture); returns (final y on the host, stats, ms)."""
+    st.init(kd, y0d, t_end, C)
+    st.step(kd, 8)
     yd = y0d.clone()
-    st.integrate(kd, yd, 1e-3 * t_end, C, stats)
-    stream = torch.cuda.current_stream(dev)
-    yd.copy_(y0d)
     _, ms = timed(lambda: st.integrate(kd, yd, t_end, C, stats), stream)
-    s = B.stats_to_numpy(stats)
-    launches, _, _ = st.timing()
-    st.close()
-    return {"cells": C, "value": float(s["steps"].sum()) / (ms * 1e-3), "unit": UNIT, "ms": ms,
-            "steps_per_cell": float(s["steps"].mean()), "cells_ok": int((s["status"] == 0).sum())}
+    return yd[:, :C].cpu().numpy(), B.stats_to_numpy(stats), ms
+
+
+def species_error(y, truth, names):
+    """Per species over the sampled cells: largest and median relative error
+    for abundances above 1e-20 in the reference solution."""
+    import numpy as np
+    live = truth > 1e-20
+    rel = np.where(live, np.abs(y - truth) / np.where(live, truth, 1.0), np.nan)
+    ok = live.any(axis=1)
+    mx = np.array([np.nanmax(r) if o else -1.0 for r, o in zip(rel, ok)])
+    med = np.array([np.nanmedian(r) if o else -1.0 for r, o in zip(rel, ok)])
+    worst = np.argsort(-mx)[:5]
+    return {"species_scored": int(ok.sum()), "max_rel": float(mx[ok].max()),
+            "median_of_species_max": float(np.median(mx[ok])),
+            "median_of_species_median": float(np.median(med[ok])),
+            "worst": [[names[i], float(mx[i]), float(med[i])] for i in worst],
+            "per_species": {names[i]: [float(mx[i]), float(med[i])] for i in range(len(names)) if ok[i]}}
+
+
+def fp64_vs_mixed(B, C, dev):
+    """The mixed-precision workload: C cells (the first C of the headline
+    stream) integrated to 1e6 yr at rtol 1e-6 in the plain FP64 mode and in
+    the mixed mode, each timed with CUDA events over one whole integration;
+    per-species max / median relative error of both (and of the oracle's own
+    rtol-1e-6 solution) against the oracle's rtol-1e-10 solution on the 32
+    stiffness-stratified cells stored in tests/golden (written by
+    make_integrate_truth.py, which calls only the oracle)."""
+    import numpy as np
+    import torch
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS[MIXED_WORKLOAD]
+    d, T, nH, Av, y0 = make(MIXED_WORKLOAD, cells=C)
+    with open(STRAT_FILE) as fh:
+        ref = json.load(fh)
+    cells = [c for c in ref["cells"] if c < C]
+    sel = [i for i, c in enumerate(ref["cells"]) if c < C]
+    truth = np.array(ref["y"]).T[:, sel]
+    net = B.Network(d, dev.index or 0)
+    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": MIXED_WORKLOAD, "cells": C, "t_end_yr": w.t_end / YEAR, "rtol": w.rtol,
+           "reference": "oracle BDF at rtol 1e-10 (tests/golden/integrate_truth_strat.json)",
+           "sampled_cells": cells,
+           "oracle_rtol6": species_error(np.array(ref["y_rtol6"]).T[:, sel], truth, d.names)}
+    for prec in ("fp64", "mixed"):
+        st = B.State(net, C, precision=prec)
+        stats = B.stats_tensor(C, dev)
+        y, s, ms = integrate_timed(B, st, kd, y0d, w.t_end, C, stats, stream)
+        st.close()
+        out[prec] = {"value": float(s["steps"].sum()) / (ms * 1e-3), "unit": UNIT, "ms": ms,
+                     "steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
+                     "newton_per_step": float(s["newton_iters"].sum() / max(s["steps"].sum(), 1)),
+                     "jac_per_step": float(s["jac_evals"].sum() / max(s["steps"].sum(), 1)),
+                     "cells_ok": int((s["status"] == 0).sum()),
+                     "error_vs_oracle": species_error(y[:, cells], truth, d.names)}
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    for key in ("fp64", "mixed", "oracle_rtol6"):
+        e = out[key] if key == "oracle_rtol6" else out[key]["error_vs_oracle"]
+        e.pop("per_species")
+    net.close()
+    return out
 
 
 RHS_GRID = [("crs", "none", 1, 1), ("crs", "nnz", 1, 1), ("crs", "rcm", 1, 1), ("coo", "none", 1, 1),
@@ -264,7 +439,8 @@ def rhs_jac_grid(B, C, dev, peaks):
     """rhs_eval for every storage format x row order of the grid and jac_eval,
     on the RHS workload (470 x 6000, C cells, log-uniform abundances): median
     of 20 CUDA-event-timed calls, L2 flushed (256 MB write) before each.
-    Algorithmic bytes and FP64 flops per cell come from sm_net_get_info."""
+    Algorithmic bytes and FP64 flops per cell come from sm_net_get_info; the
+    binding ceiling is min(HBM bandwidth x intensity, FP64 peak)."""
     import numpy as np
     import torch
     from synth.workloads import make
@@ -289,8 +465,9 @@ def rhs_jac_grid(B, C, dev, peaks):
     def row(kind, ms, nbytes, flops):
         gbs = nbytes * C / (ms * 1e-3) / 1e9
         tf = flops * C / (ms * 1e-3) / 1e12
+        ceiling = min(peaks["hbm_gbs"] * 1e9 * flops / nbytes / 1e12, peaks["fp64_tflops"])
         return {"kind": kind, "us": ms * 1e3, "GB_s": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
-                "fp64_TF_s": tf, "fp64_frac": tf / peaks["fp64_tflops"]}
+                "fp64_TF_s": tf, "fp64_frac": tf / peaks["fp64_tflops"], "binding_frac": tf / ceiling}
 
     out = []
     for fmt in RHS_GRID:
@@ -302,72 +479,31 @@ def rhs_jac_grid(B, C, dev, peaks):
     out.append(row("jac", ms, info["jac_bytes"], info["jac_flops"]))
     net.sync()
     net.close()
+    best = max((r for r in out if r["kind"].startswith("rhs")), key=lambda r: r["binding_frac"])
     return {"workload": "rhs_jac_470x6000_c4096", "cells": C, "l2": "flushed before every call",
             "rhs_bytes_per_cell": info["rhs_bytes"], "rhs_flops_per_cell": info["rhs_flops"],
             "jac_bytes_per_cell": info["jac_bytes"], "jac_flops_per_cell": info["jac_flops"],
-            "peaks": peaks, "rows": out}
+            "peaks": peaks, "best_rhs": best["kind"], "best_rhs_binding_frac": best["binding_frac"],
+            "rows": out}
 
 
-def measured_peaks():
-    """HBM copy bandwidth from the measured-peaks file when present; the FP64
-    rate is our own FMA probe (1.19 TFLOP/s on this machine's GB300)."""
-    hbm = 6790.0
+def peaks_(B, dev):
+    """HBM: the measured copy bandwidth (MEASURED_PEAKS.json); FP64 / FP32:
+    unit counts x clock, with this run's FMA-probe rates beside them."""
+    hbm, src = 6782.4, "fallback"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            mp = json.load(fh)
-        hbm = float(mp.get("hbm_gbs", hbm))
-    except (OSError, ValueError):
+            hbm, src = float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json"
+    except (OSError, ValueError, KeyError):
         pass
-    return {"hbm_gbs": hbm, "fp64_tflops": 1.19}
-
-
-def accuracy_vs_oracle(B, dev, full=False):
-    """Final abundances of the four stored 470 x 6000 cells (T 10-1000 K, n_H
-    1e2-1e8, A_V 0-20, atomic start, 1e6 yr) in every precision, against the
-    oracle's rtol-1e-10 solution stored in tests/golden (written by
-    make_integrate_truth.py, which calls only the oracle).  Per species: the
-    largest and the median relative error over the cells, for abundances
-    above 1e-20; the oracle's own rtol-1e-6 solution is scored the same way."""
-    import numpy as np
-    import torch
-    from synth import cells as sc
-    from synth import network as sn
-    with open(os.path.join(ROOT, "tests", "golden", "integrate_truth_large.json")) as fh:
-        ref = json.load(fh)
-    truth = np.array(ref["y"]).T
-    n_s, C = truth.shape
-    d = sn.generate(2312, 470, 6000)
-    T, nH, Av = sc.conditions(4998, C, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0))
-    y0 = sc.atomic_start(d, C)
-    net = B.Network(d, dev.index or 0)
-    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
-    live = truth > 1e-20
-
-    def score(y):
-        rel = np.where(live, np.abs(y - truth) / np.where(live, truth, 1.0), np.nan)
-        mx = np.nanmax(np.where(np.isnan(rel), -1.0, rel), axis=1)
-        med = np.array([np.median(r[~np.isnan(r)]) if np.any(~np.isnan(r)) else -1.0 for r in rel])
-        ok = mx >= 0
-        worst = np.argsort(-mx)[:5]
-        out = {"max_rel": float(mx[ok].max()), "median_of_species_medians": float(np.median(med[ok])),
-               "species_scored": int(ok.sum()),
-               "worst": [[d.names[i], float(mx[i])] for i in worst]}
-        if full:
-            out["per_species"] = {d.names[i]: [float(mx[i]), float(med[i])] for i in range(n_s) if ok[i]}
-        return out
-
-    res = {"cells": C, "reference": "oracle BDF at rtol 1e-10 (tests/golden/integrate_truth_large.json)",
-           "oracle_rtol6": score(np.array(ref["y_rtol6"]).T)}
-    for prec in ("fp64", "mixed", "tf32"):
-        st = B.State(net, C, precision=prec)
-        yd = y0d.clone()
-        code = st.integrate(kd, yd, 1e6 * YEAR, C)
-        torch.cuda.synchronize()
-        res[prec] = score(yd.cpu().numpy()[:, :C])
-        res[prec]["status"] = int(code)
-        st.close()
-    net.close()
-    return res
+    out = {"hbm_gbs": hbm, "hbm_source": src, "fp64_tflops": PEAK_FP64, "fp32_tflops": PEAK_FP32,
+           "alu_source": "152 SMs x 2.07 GHz x (FP64 4 | FP32 256) flops/clk"}
+    try:
+        out["probe_fp64_tflops"] = B.probe_fma(dev.index or 0, True)
+        out["probe_fp32_tflops"] = B.probe_fma(dev.index or 0, False)
+    except Exception as exc:  # noqa: BLE001
+        out["probe_error"] = f"{type(exc).__name__}: {exc}"
+    return out
 
 
 def adjoint_measurement(B, C, dev):
@@ -386,13 +522,9 @@ def adjoint_measurement(B, C, dev):
     st = B.State(net, C, precision="fp64", record_steps=8000)
     kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
     stats = B.stats_tensor(C, dev)
-    yd = y0d.clone()
     stream = torch.cuda.current_stream(dev)
-    st.integrate(kd, yd, 1e-3 * t_end, C, stats)      # warm-up (graph capture)
-    yd.copy_(y0d)
-    code_f, f_ms = timed(lambda: st.integrate(kd, yd, t_end, C, stats), stream)
-    s = B.stats_to_numpy(stats)
-    yN = yd.cpu().numpy()[:, :C]
+    yN, s, f_ms = integrate_timed(B, st, kd, y0d, t_end, C, stats, stream)
+    code_f = int((s["status"] != 0).any())
     ld = B.pad_ld(C)
     frac = (yN > 1e-12).mean(axis=1)
     targets = np.argsort(-frac, kind="stable")[:8]
@@ -409,7 +541,7 @@ def adjoint_measurement(B, C, dev):
            "targets": [d.names[t] for t in targets], "forward_ms": f_ms, "adjoint_ms": a_ms,
            "adjoint_per_forward": a_ms / f_ms, "adjoint_ms_per_target": a_ms / 8,
            "steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
-           "cells_ok": int((astat.cpu().numpy()[:C] == 0).sum()), "forward_status": int(code_f),
+           "cells_ok": int((astat.cpu().numpy()[:C] == 0).sum()), "forward_partial": code_f,
            "adjoint_status": int(code_a), "adjoint_launches": int(l1 - l0),
            "checkpoint_every": B.CHECKPOINT_EVERY}
     st.close()
@@ -424,11 +556,43 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def roofline(info, s, kind, precision, kern_ms, kern_n, peaks):
+    """Roofline of the timed kernel class over the timed integration."""
+    if not kern_n:
+        return None
+    refreshes = float(s["jac_evals"].sum())
+    newton = float(s["newton_iters"].sum())
+    if kind == "refresh":
+        # per refreshed cell: J gather (2 flops per term) + M assembly + LU
+        unit = 2.0 * info["n_jac_terms"] + 2.0 * info["nnz_J"] + float(info["lu_flops"])
+        units = refreshes
+        fp32 = precision != "fp64"
+    elif kind == "rhs":
+        unit, units, fp32 = info["rhs_flops"], newton, False
+    else:
+        return None
+    per_launch_units = units / kern_n
+    avg_s = kern_ms * 1e-3 / kern_n
+    ach = unit * per_launch_units / avg_s / 1e12
+    pk = peaks["fp32_tflops"] if fp32 else peaks["fp64_tflops"]
+    tr = TRAFFIC.get((kind, precision, kernel_source_hash()))
+    return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": None if tr is None else tr * per_launch_units,
+            "kernel": f"{kind} ({'FP32' if fp32 else 'FP64'} pipe)", "avg_launch_ms": kern_ms / kern_n,
+            "timed_launches": kern_n, "units_per_launch": per_launch_units,
+            "flops_per_unit": unit, "unit_name": "refreshed cell" if kind == "refresh" else "cell RHS",
+            "peak_source": peaks["alu_source"]}
+
+
 def main():
+    t_start = time.time()
     a = args_()
     rank, world, local = dist_env()
     if a.impl == "reference":
         return reference_arm(a, rank)
+    if a.only == "cpu":
+        print(json.dumps(cpu_baseline(a.t_end_yr * YEAR)))
+        return
     import numpy as np
     import torch
 
@@ -439,13 +603,13 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if a.rhs_only:
+    if a.only:
+        fn = {"rhs": lambda: rhs_jac_grid(B, a.rhs_cells, dev, peaks_(B, dev)),
+              "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
+              "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
+              "probe": lambda: peaks_(B, dev)}[a.only]
         if rank == 0:
-            print(json.dumps(rhs_jac_grid(B, a.rhs_cells, dev, measured_peaks())))
-        return
-    if a.accuracy_only:
-        if rank == 0:
-            print(json.dumps(accuracy_vs_oracle(B, dev, full=True)))
+            print(json.dumps(fn()))
         return
     if world > 1:
         import torch.distributed as dist
@@ -460,55 +624,66 @@ def main():
     info = net.info()
     state = B.State(net, C, precision=a.precision, timing_kind=a.time_kernel)
     ld = B.pad_ld(C)
-
-    def padded(v, fill):
-        out = torch.full((ld,), fill, dtype=torch.float64, device=dev)
-        out[:C] = torch.tensor(v, dtype=torch.float64, device=dev)
-        return out
-
-    Td, nHd, Avd = padded(T, 100.0), padded(nH, 1.0), padded(Av, 0.0)
+    Td, nHd, Avd = device_conditions(B, T, nH, Av, dev)
     y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
     y0d[:, :C] = torch.tensor(y0, dtype=torch.float64, device=dev)
     kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
-    yd = torch.empty_like(y0d)
     stats = B.stats_tensor(C, dev)
+    per = state.opts.attempts_per_sync
+    A = slice_attempts(a.attempts_est, a.steps, per)
 
-    def step():
-        net.rates_eval(Td, nHd, Avd, kd, C)
-        yd.copy_(y0d)
-        state.integrate(kd, yd, t_end, C, stats)
-        s = B.stats_to_numpy(stats)
-        return int(s["steps"].sum()), s
+    def step(s):
+        """Bench step s of K: a slice of the integration (see the module
+        docstring)."""
+        if s == 0:
+            net.rates_eval(Td, nHd, Avd, kd, C)
+            state.init(kd, y0d, t_end, C)
+        if s < a.steps - 1:
+            state.step(kd, A)
+            return 0
+        n = 0
+        while state.read() > 0 and n < MAX_TAIL_ATTEMPTS:
+            state.step(kd, per)
+            n += per
+        return n
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
+    # warm-up: the first slices of a separate integration of the same batch
+    net.rates_eval(Td, nHd, Avd, kd, C)
+    state.init(kd, y0d, t_end, C)
     for _ in range(a.warmup):
-        step()
+        state.step(kd, A)
+    torch.cuda.synchronize()
     clk = clocks_start(local)
     barrier()
     torch.cuda.synchronize()
     state.timing_reset()
+    l_before, _, _ = state.timing()
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cell_steps = 0
-    last = None
-    for _ in range(a.steps):
-        n, last = step()
-        cell_steps += n
+    tail = 0
+    for s in range(a.steps):
+        tail = step(s)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = clocks_stop(clk)
     ms = e0.elapsed_time(e1)
-    launches, kern_ms, kern_n = state.timing()
-    launches += a.steps       # the state counts its own kernels; add one rates_eval per step
-    cell_steps, ms = combine_ranks(cell_steps, ms, world, dev)
-    value = cell_steps / (ms * 1e-3)
+    l_after, kern_ms, kern_n = state.timing()
+    launches = l_after - l_before + 1          # + the rates_eval of step 1
+    state.read(stats=stats)
+    s = B.stats_to_numpy(stats)
+    cell_steps = int(s["steps"].sum())
+    attempts = int((s["steps"] + s["rejects"] + s["conv_fails"]).max())
+    cell_steps_all, ms_max = combine_ranks(cell_steps, ms, world, dev)
+    value = cell_steps_all / (ms_max * 1e-3)
 
-    # end to end through the public calls with host buffers
+    # end to end through the public calls with host buffers: one whole
+    # integration (inputs copied in, solution and per-cell results copied out)
     e2e = None
     if not a.no_e2e:
         hT = torch.tensor(T, dtype=torch.float64).pin_memory()
@@ -519,96 +694,70 @@ def main():
         hy0 = hy0.pin_memory()
         hy = torch.empty_like(hy0).pin_memory()
         hst = torch.empty(stats.numel(), dtype=torch.uint8).pin_memory()
+        yd = torch.empty_like(y0d)
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        e2e_steps = 0
-        for _ in range(a.steps):
-            Td[:C].copy_(hT, non_blocking=True)
-            nHd[:C].copy_(hnH, non_blocking=True)
-            Avd[:C].copy_(hAv, non_blocking=True)
-            yd.copy_(hy0, non_blocking=True)
-            net.rates_eval(Td, nHd, Avd, kd, C)
-            state.integrate(kd, yd, t_end, C, stats)
-            hy.copy_(yd, non_blocking=True)
-            hst.copy_(stats, non_blocking=True)
-            torch.cuda.synchronize()
-            e2e_steps += int(np.frombuffer(hst.numpy().tobytes(), dtype=B.CELL_STATS_DTYPE)["steps"].sum())
+        Td[:C].copy_(hT, non_blocking=True)
+        nHd[:C].copy_(hnH, non_blocking=True)
+        Avd[:C].copy_(hAv, non_blocking=True)
+        yd.copy_(hy0, non_blocking=True)
+        net.rates_eval(Td, nHd, Avd, kd, C)
+        state.integrate(kd, yd, t_end, C, stats)
+        hy.copy_(yd, non_blocking=True)
+        hst.copy_(stats, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
         e_ms = f0.elapsed_time(f1)
-        e2e_steps, e_ms = combine_ranks(e2e_steps, e_ms, world, dev)
-        e2e = {"value": e2e_steps / (e_ms * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": int(C * (3 + d.n_s) * 8),
-               "d2h_bytes_per_step": int(d.n_s * ld * 8 + stats.numel())}
-
+        e_steps = int(np.frombuffer(hst.numpy().tobytes(), dtype=B.CELL_STATS_DTYPE)["steps"].sum())
+        e_steps, e_ms = combine_ranks(e_steps, e_ms, world, dev)
+        e2e = {"value": e_steps / (e_ms * 1e-3), "unit": UNIT, "steps": 1,
+               "h2d_bytes_per_step": int(3 * C * 8 + hy0.numel() * 8),
+               "d2h_bytes_per_step": int(hy.numel() * 8 + hst.numel()),
+               "what": "one whole integration of the batch: host conditions and y0 copied in, "
+                       "sm_rates_eval + sm_integrate, solution and per-cell results copied out"}
+    state.close()
     if rank != 0:
         return
-    # roofline of the timed kernel class
-    s = last
-    jac = float(s["jac_evals"].sum())
-    newton = float(s["newton_iters"].sum())
-    per_launch_flops = None
-    if kern_n:
-        if a.time_kernel == "refresh":
-            # per refreshed cell: J gather (2 flops per term) + M assembly + LU
-            unit = 2.0 * info["n_jac_terms"] + 2.0 * info["nnz_J"] + float(info["lu_flops"])
-            per_launch_flops = unit * jac * a.steps / kern_n
-        elif a.time_kernel == "rhs":
-            per_launch_flops = info["rhs_flops"] * newton * a.steps / kern_n
-    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
-    peak_fp64 = 152 * 4 * 2.07e9 / 1e12
-    roof = None
-    if per_launch_flops is not None:
-        avg_s = kern_ms * 1e-3 / kern_n
-        ach = per_launch_flops / avg_s / 1e12
-        fp32 = a.precision != "fp64" and a.time_kernel == "refresh"
-        pk = peak_fp32 if fp32 else peak_fp64
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": TRAFFIC.get((a.time_kernel, a.precision, kernel_source_hash())),
-                "kernel": f"{a.time_kernel} ({'FP32' if fp32 else 'FP64'} pipe)",
-                "avg_launch_ms": kern_ms / kern_n, "timed_launches": kern_n,
-                "peak_source": "unit counts x 2.07 GHz max SM clock: FP32 152x128x2, FP64 152x4 flops/clk"}
+
     def aux(fn, *args):
         # the auxiliary measurements must not cost the main line
+        if time.time() - t_start > a.budget_s:
+            return {"skipped": f"run older than --budget-s {a.budget_s:.0f} s"}
         try:
             return fn(*args)
         except Exception as exc:  # noqa: BLE001
             return {"error": f"{type(exc).__name__}: {exc}"}
 
-    fp64 = None
-    if a.fp64_cells > 0 and a.precision != "fp64":
-        n = min(a.fp64_cells, C)
-        fp64 = aux(fp64_comparison, B, net, d, T[:n], nH[:n], Av[:n], np.ascontiguousarray(y0[:, :n]), t_end,
-                   dev)
-    del state
+    peaks = aux(peaks_, B, dev)
+    roof = roofline(info, s, a.time_kernel, a.precision, kern_ms, kern_n, peaks)
+    if roof is not None:
+        roof["peak_kind"] = "derived (unit counts x max clock), timed inside a long step"
+    mixed = aux(fp64_vs_mixed, B, a.mixed_cells, dev) if a.mixed_cells > 0 else None
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
-    rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, measured_peaks()) if a.rhs_cells > 0 else None
-    acc = None if a.no_accuracy else aux(accuracy_vs_oracle, B, dev)
-    cpu = None
-    if not a.no_cpu:
-        n = a.cpu_cells or host_cores()
-        st_, dt_, cores = oracle_sample(n, t_end, 0)
-        cpu = {"value": st_ / dt_, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {n} cells of {WORKLOAD}, first {CPU_STEPS} accepted steps of each "
-                         f"from the atomic start, one single-threaded process per cell ({dt_:.1f} s)"}
+    rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
+    cpu = None if a.no_cpu else aux(cpu_baseline, t_end)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32", "tf32": "f64+f32+tf32"}[a.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells_per_gpu": C, "n_s": d.n_s, "n_r": d.n_r,
                    "t_end_yr": a.t_end_yr, "rtol": 1e-6, "atol": 1e-20, "precision": a.precision,
-                   "inputs": "larger than L2 (k' alone is 3.1 GB per GPU)"},
-        "stats": {"steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
+                   "step": f"one slice of one whole integration: {A} attempts per step, the last step until "
+                           f"every cell reached t_end ({tail} attempts)",
+                   "l2": "inputs larger than L2 (k' alone is 3.1 GB per GPU)"},
+        "stats": {"cell_steps": cell_steps, "steps_per_cell": float(s["steps"].mean()),
+                  "max_steps": int(s["steps"].max()), "attempts": attempts,
                   "newton_per_cell": float(s["newton_iters"].mean()),
                   "jac_per_cell": float(s["jac_evals"].mean()),
                   "rejects_per_cell": float(s["rejects"].mean()),
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64": fp64, "adjoint": adj, "rhs_jac": rhs, "accuracy": acc,
+        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "peaks": peaks,
+        "wall_s": time.time() - t_start,
     }
     print(json.dumps(out))
 

@@ -158,8 +158,11 @@ typedef struct {
  * one warm-up and five calls with CUDA events on `stream` (median), and leaves
  * the fastest selected (as sm_net_set_format would).  The choice is cached for
  * the process per (network content, device name, C rounded up to a power of
- * two); force = 1 measures again.  Synchronises with `stream`.  SM_EINVAL on
- * bad arguments or a host-only network. */
+ * two); force = 1 measures again.  Synchronises with `stream`.  d_f is
+ * scratch: it holds the last candidate's result on return.  If a candidate
+ * fails (SM_ENOMEM, SM_ECUDA), the traversal selected before the call is
+ * restored and the error returned.  SM_EINVAL on bad arguments or a
+ * host-only network. */
 sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, const double* d_y, double* d_f,
                           int64_t ld, int32_t force, void* stream, sm_tune_result* out);
 
@@ -199,21 +202,22 @@ sm_status sm_rhs_eval(const sm_net* net, int64_t C, const double* d_k, const dou
                       double* d_f, int64_t ld, void* stream);
 
 /* Right-hand side without any device allocation.  Same inputs, outputs,
- * formats and results as sm_rhs_eval, for callers that cannot allow a library
- * to call cudaMalloc: code that runs while a stream is being captured into a
- * CUDA graph (allocation is not permitted there), and host codes that reserve
- * the device memory up front for their own pool.  The per-reaction rate
- * buffer lives in one fixed array compiled into the library
+ * formats and results as sm_rhs_eval, for callers that cannot let a library
+ * call cudaMalloc: hydro codes that reserve the device memory up front for
+ * their own pool allocator (an allocation from inside the chemistry call
+ * would fail or take memory the pool counts on), and codes whose time-step
+ * loop must not allocate because cudaMalloc can synchronise the device.  The
+ * per-reaction rate buffer lives in one fixed array compiled into the library
  * (SM_STATIC_SCRATCH_DOUBLES doubles, 32 MiB, held by every GPU that loads
  * the library until the process exits); requests with
  * n_r * round_up(C, 32) > SM_STATIC_SCRATCH_DOUBLES return SM_ETOOBIG.
- * The first call on a device looks up that array's device address (and loads
- * the coefficient table), so make it once before any stream capture.  Every
- * call on a device shares the array: calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * The array keeps the last call's contents; nothing in it needs to start at
- * zero because each call writes every value it reads.
- * The paper has no counterpart to this entry point. */
+ * The first call on a device looks up that array's device address (a
+ * set-up step done once per device), so make that first call before any
+ * stream capture.  Every call on a device shares the array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The array keeps the last call's contents;
+ * nothing in it needs to start at zero because each call writes every value
+ * it reads.  The paper has no counterpart to this entry point. */
 #define SM_STATIC_SCRATCH_DOUBLES 4194304
 sm_status sm_rhs_eval_static(const sm_net* net, int64_t C, const double* d_k, const double* d_y,
                              double* d_f, int64_t ld, void* stream);
@@ -419,6 +423,16 @@ sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* 
  * the workspace is the cotangent-free part). */
 sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, int32_t* d_astat,
                     int64_t cells_per_pass, void* stream);
+
+/* Measured arithmetic throughput of the device's FMA pipes (the ceilings
+ * of the FP64-bound right-hand side, Jacobian and residual and of the
+ * FP32 factorisation, Section 5's roofline analysis carried to this GPU):
+ * fp64 = 1 probes FP64, 0 probes FP32.  Every thread of several CTAs per SM
+ * runs eight independent FMA chains (2 flops each), timed with CUDA events
+ * over three launches after a warm-up; *tflops receives the best rate in
+ * TFLOP/s.  Allocates and frees a small device buffer, synchronises the
+ * device's legacy stream.  SM_EINVAL on a NULL pointer or negative device. */
+sm_status sm_probe_fma(int32_t device, int32_t fp64, double* tflops);
 
 /* Wait for all work on `stream` and report (and clear) any error a kernel of
  * this network wrote to its device status word. */

@@ -261,7 +261,8 @@ def integrate_cell(desc, k, y0, t_end, opts: BDFOptions = BDFOptions(), S=None,
                 if eta_hi > best_eta:
                     best_eta, best_q = eta_hi, q + 1
         if record:
-            res.log.append(dict(t=t, h=h, q=q, refresh=refresh, iters=n_it, outcome="accept", err=err))
+            res.log.append(dict(t=t, h=h, q=q, refresh=refresh, iters=n_it, outcome="accept", err=err,
+                                y=y.copy()))
         t = t_new
         Y.insert(0, y)
         T.insert(0, t_new)
@@ -283,6 +284,33 @@ def integrate_cell(desc, k, y0, t_end, opts: BDFOptions = BDFOptions(), S=None,
         rejected = False
     res.y, res.t, res.h_last, res.q_last = Y[0], t, h, q
     return res
+
+
+def solve_step(desc, k, hist_y, hist_t, t_new, h, S=None, tol=1e-14, max_iter=30, y_start=None):
+    """Exact solution of one step's implicit BDF equation given its history.
+
+    hist_y / hist_t: the q past solutions and times, newest first (y_{n},
+    y_{n-1}, ...; the order is q = len(hist_y)); the step ends at t_new with
+    size h.  Solves alpha_0 y + sum_{i=1..q} alpha_i y_{n+1-i} - h f(y) = 0
+    (alpha_i = h l_i'(t_new) on the nodes t_new, hist_t) by full Newton with
+    a fresh Jacobian every iteration until max |delta_i| / |y_i| <= tol
+    (components that are exactly zero compared absolutely).  Starts from
+    y_start, else from hist_y[0]."""
+    if S is None:
+        S = stoichiometry(desc)
+    k = np.asarray(k, dtype=float)
+    q = len(hist_y)
+    alpha = bdf_alphas([t_new] + list(hist_t[:q]), h)
+    psi = sum(alpha[i] * np.asarray(hist_y[i - 1], dtype=float) for i in range(1, q + 1))
+    y = np.array(hist_y[0] if y_start is None else y_start, dtype=float)
+    I = np.eye(desc.n_s)
+    for _ in range(max_iter):
+        G = alpha[0] * y + psi - h * (S @ reaction_rates(desc, k, y))
+        delta = np.linalg.solve(alpha[0] * I - h * jacobian(desc, k, y, S), -G)
+        y = y + delta
+        if np.all(np.abs(delta) <= tol * np.abs(y)):
+            break
+    return y
 
 
 def integrate(desc, k, y0, t_end, opts: BDFOptions = BDFOptions(), cells=None):

@@ -95,6 +95,7 @@ _SIGS = [
     ("sm_jac_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_int64, ct.c_void_p]),
     ("sm_sync", ct.c_int32, [ct.c_void_p, ct.c_void_p]),
+    ("sm_probe_fma", ct.c_int32, [ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double)]),
     ("sm_opts_default", None, [ct.POINTER(Opts_c)]),
     ("sm_state_create", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.POINTER(Opts_c), ct.POINTER(ct.c_void_p)]),
     ("sm_state_free", ct.c_int32, [ct.c_void_p]),
@@ -438,6 +439,13 @@ class State:
             return code
         _check(code, "sm_replay")
         return code
+
+
+def probe_fma(device: int, fp64: bool) -> float:
+    """Measured FMA throughput of the FP64 (fp64=True) or FP32 pipe, TFLOP/s."""
+    v = ct.c_double()
+    _check(lib().sm_probe_fma(int(device), int(bool(fp64)), ct.byref(v)), "sm_probe_fma")
+    return v.value
 
 
 def stats_tensor(C, device):

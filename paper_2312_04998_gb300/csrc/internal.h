@@ -136,6 +136,9 @@ sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double
 sm_status launch_rhs_masked(const sm_net* net, int64_t C, const double* k, int64_t ldk,
                             const double* y, double* f, int64_t ld, double* scratch, int64_t ldr,
                             const int* mask, int bit, cudaStream_t s);
+// Per-device set-up of the right-hand-side kernels (constant tables); called
+// when a network is uploaded.
+sm_status rhs_prepare_device(int device);
 sm_status launch_jac(const sm_net* net, int64_t C, const double* k, const double* y,
                      double* J, int64_t ld, cudaStream_t s);
 

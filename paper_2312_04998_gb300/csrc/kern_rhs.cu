@@ -13,6 +13,9 @@
 //    the slice column-major, pads included.
 // In every traversal a lane owns one cell: index loads are warp-uniform
 // broadcasts and abundance / rate loads are 128-byte coalesced rows.
+#include <atomic>
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -192,15 +195,34 @@ __global__ void rhs_sell_kernel(int64_t C, int slice_h, const int* __restrict__ 
   if (i >= 0) f[(int64_t)i * ld + c] = acc;
 }
 
-bool g_coef_ready[64] = {false};
+constexpr int kMaxDevices = 64;
+std::atomic<bool> g_coef_ready[kMaxDevices];
+std::mutex g_coef_mu;
 
-sm_status ensure_coef_table(int device) {
-  if (device >= 0 && device < 64 && g_coef_ready[device]) return SM_OK;
+}  // namespace
+
+// Loads the coefficient decode table into `device`'s constant memory (the
+// device must be current).  Called once per device when a network is built,
+// so that the right-hand-side launches never issue this synchronous copy;
+// thread-safe.
+sm_status rhs_prepare_device(int device) {
+  if (device < 0 || device >= kMaxDevices) return SM_EINVAL;
+  if (g_coef_ready[device].load(std::memory_order_acquire)) return SM_OK;
+  std::lock_guard<std::mutex> lock(g_coef_mu);
+  if (g_coef_ready[device].load(std::memory_order_relaxed)) return SM_OK;
   double t[256];
   for (int i = 0; i < 256; ++i) t[i] = (double)(int8_t)i;
   SM_TRY_CUDA(cudaMemcpyToSymbol(c_coef, t, sizeof(t)));
-  if (device >= 0 && device < 64) g_coef_ready[device] = true;
+  g_coef_ready[device].store(true, std::memory_order_release);
   return SM_OK;
+}
+
+namespace {
+
+sm_status ensure_coef_table(int device) {
+  if (device >= 0 && device < kMaxDevices && g_coef_ready[device].load(std::memory_order_acquire))
+    return SM_OK;
+  return rhs_prepare_device(device);
 }
 
 }  // namespace

@@ -596,6 +596,7 @@ sm_status net_upload(sm_net* net) {
     rate[4 * j + 3] = (double)c;
   }
   sm_status st;
+  if ((st = rhs_prepare_device(net->device)) != SM_OK) return st;
   if ((st = net->d_reac.upload(reac2.data(), reac2.size() * 4)) != SM_OK) return st;
   if ((st = net->d_rate.upload(rate.data(), rate.size() * 8)) != SM_OK) return st;
   // Jacobian gather words: reaction (low 23 bits) | partner+1 ... packed as two

@@ -1,7 +1,8 @@
 // sm_rhs_eval_static: the right-hand side with its per-reaction rate buffer
 // in a fixed array compiled into the library, for callers that cannot let the
-// library allocate device memory (stream capture, pre-reserved memory pools).
-// The kernels are the same as sm_rhs_eval's; only the buffer differs.
+// library allocate device memory (codes that pre-reserve the device memory for
+// their own pool, time-step loops that must not allocate).  The kernels are
+// the same as sm_rhs_eval's; only the buffer differs.
 #include <mutex>
 
 #include "internal.h"

@@ -136,6 +136,8 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
     }
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Format& cur = net->cur;
+  const Candidate prev{cur.fmt, cur.order, cur.C, cur.sigma};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SM_TRY_CUDA(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -160,7 +162,11 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st != SM_OK) return st;
+  if (st != SM_OK) {
+    // leave the caller's traversal selected, not the failing candidate's
+    net_select_format(net, prev.fmt, prev.order, prev.C, prev.sigma);
+    return st;
+  }
   best.candidates = (int32_t)grid.size();
   best.cached = 0;
   if ((st = net_select_format(net, best.fmt, best.order, best.sell_C, best.sell_sigma)) != SM_OK) return st;

@@ -2,7 +2,13 @@
 the integrator tests: the oracle's BDF method at rtol 1e-10 / atol 1e-24 on
 seeded synthetic cells.  Calls only the oracle and the input generators.
 
-    python tests/golden/make_integrate_truth.py [small|large|all]
+    python tests/golden/make_integrate_truth.py [small|large|strat|all]
+
+The "strat" case is a stiffness-stratified sample of the 16,384-cell
+mixed-precision workload (470 x 6000, T 10-1000 K, n_H 1e2-1e8, A_V 0-20,
+atomic start, 1e6 yr): every 128th of its cells is integrated by the oracle
+at rtol 1e-6, and the 32 cells at evenly spaced quantiles of those step
+counts are kept.
 """
 import json
 import multiprocessing as mp
@@ -24,27 +30,63 @@ CASES = {
     # name: (n_s, n_r, cells, T range, nH range, Av range, t_end)
     "small": (32, 180, 24, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0), 1e6 * YEAR),
     "large": (470, 6000, 4, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0), 1e6 * YEAR),
+    "strat": (470, 6000, 32, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0), 1e6 * YEAR),
 }
 
 
-def case_inputs(name):
-    n_s, n_r, C, Tr, nr, ar, t_end = CASES[name]
+STRAT_POOL = 16384      # cells of the workload the stratified sample is drawn from
+STRAT_STRIDE = 128      # every 128th cell is a candidate
+STRAT_CELLS = 32
+
+
+def case_inputs(name, C=None, cells=None):
+    """(desc, k'[n_r, len(cells)], y0, t_end) for the given cells (default:
+    all) of the case's first C cells."""
+    n_s, n_r, C0, Tr, nr, ar, t_end = CASES[name]
+    C = C0 if C is None else C
+    cells = np.arange(C) if cells is None else np.asarray(cells)
     d = sn.generate(2312, n_s, n_r)
     T, nH, Av = sc.conditions(4998, C, Tr, nr, ar)
-    return d, ok.rate_coefficients(d, T, nH, Av), sc.atomic_start(d, C), t_end
+    T, nH, Av = T[cells], nH[cells], Av[cells]
+    return d, ok.rate_coefficients(d, T, nH, Av), sc.atomic_start(d, len(cells)), t_end
 
 
 def _one(args):
-    name, c, rtol, atol = args
-    d, k, y0, t_end = case_inputs(name)
-    r = ob.integrate_cell(d, k[:, c], y0[:, c], t_end, ob.BDFOptions(rtol=rtol, atol=atol))
+    name, c, rtol, atol, C = args
+    d, k, y0, t_end = case_inputs(name, C, [c])
+    r = ob.integrate_cell(d, k[:, 0], y0[:, 0], t_end, ob.BDFOptions(rtol=rtol, atol=atol))
     return c, r.y.tolist(), r.status, r.steps
 
 
-def _solve_all(name, rtol, atol):
-    C = CASES[name][2]
-    with mp.get_context("spawn").Pool(min(C, os.cpu_count() or 1)) as pool:
-        return sorted(pool.map(_one, [(name, c, rtol, atol) for c in range(C)]))
+def _solve_all(name, rtol, atol, cells=None, C=None):
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    cells = list(range(CASES[name][2])) if cells is None else list(cells)
+    with mp.get_context("spawn").Pool(min(len(cells), os.cpu_count() or 1)) as pool:
+        res = pool.map(_one, [(name, c, rtol, atol, C) for c in cells])
+    order = {c: i for i, c in enumerate(cells)}
+    return sorted(res, key=lambda r: order[r[0]])
+
+
+def make_strat():
+    """integrate_truth_strat.json: 32 cells of the 16,384-cell workload at
+    evenly spaced quantiles of the oracle's rtol-1e-6 step count (drawn from
+    every 128th cell), with the rtol-1e-10 solution (y), the oracle's own
+    rtol-1e-6 solution (y_rtol6) and both step counts."""
+    cand = list(range(0, STRAT_POOL, STRAT_STRIDE))
+    res6 = _solve_all("strat", 1e-6, 1e-20, cand, STRAT_POOL)
+    steps = np.array([r[3] for r in res6])
+    order = np.argsort(steps, kind="stable")
+    pick = sorted({int(order[int((i + 0.5) * len(cand) / STRAT_CELLS)]) for i in range(STRAT_CELLS)})
+    cells = [cand[i] for i in pick]
+    res10 = _solve_all("strat", 1e-10, 1e-24, cells, STRAT_POOL)
+    out = {"source": "oracle BDF at rtol 1e-10, atol 1e-24 (make_integrate_truth.py)",
+           "case": "strat", "spec": [str(v) for v in CASES["strat"]], "pool_cells": STRAT_POOL,
+           "cells": cells, "candidate_steps_rtol6": steps.tolist(),
+           "y": [r[1] for r in res10], "status": [r[2] for r in res10], "steps": [r[3] for r in res10],
+           "y_rtol6": [res6[i][1] for i in pick], "steps_rtol6": [res6[i][3] for i in pick]}
+    with open(os.path.join(HERE, "integrate_truth_strat.json"), "w") as fh:
+        json.dump(out, fh)
 
 
 def make(name, only_rtol6=False):
@@ -70,6 +112,9 @@ def make(name, only_rtol6=False):
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "all"
     only6 = "--rtol6-only" in sys.argv
-    for nm in (["small", "large"] if which == "all" else [which]):
-        make(nm, only6)
+    for nm in (["small", "large", "strat"] if which == "all" else [which]):
+        if nm == "strat":
+            make_strat()
+        else:
+            make(nm, only6)
         print("wrote", nm)

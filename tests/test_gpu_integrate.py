@@ -90,6 +90,24 @@ def load_truth(name, key="y"):
         return np.array(json.load(fh)[key]).T
 
 
+# Per-cell bar of test_large_network_matches_oracle: the GPU's error against
+# the rtol-1e-10 truth over the oracle's own rtol-1e-6 error (both in
+# tolerance units; floor one unit)
+STRAT_FACTOR = {"fp64": 3.0, "mixed": 4.0, "tf32": 4.0}
+U32 = 2.0 ** -24
+
+
+def fp32_drift_bar(stats, rtol=1e-6):
+    """Largest relative drift of an element total allowed to a reduced-
+    precision run, per cell: every Newton iteration restores E y up to the
+    error of its FP32 solve, about u32 * kappa * |delta|_wrms * rtol relative
+    (the solve runs on the WRMS-equilibrated matrix, so its error is relative
+    to the error weights rtol |y| + atol), and the residue is carried forward
+    through the history.  Summed over the cell's Newton iterations with
+    |delta| <= 1 and a conditioning allowance kappa = 1e6."""
+    return 1e-11 + stats["newton_iters"] * U32 * 1e6 * rtol
+
+
 def weighted_err(y, ref, rtol=1e-6, atol=1e-20):
     """Largest |y - ref| in units of the integrator's error weight."""
     return float(np.max(np.abs(y - ref) / (rtol * np.abs(ref) + atol)))
@@ -163,10 +181,11 @@ def test_conservation_gpu(torch, B, small_case, moderate_case, case, precision):
     conditioning, lets them drift, and the oracle (LAPACK, pivoted FP64)
     drifts too: up to 3e-10 relative on the moderate cells, 7e-7 on the stiff
     24-cell case (T to 1000 K, n_H to 1e8, 1e6 yr).  FP64 must stay within 4x
-    the oracle's drift on the same cells, per element (floor 1e-13).  Mixed
-    precision rounds each Newton correction to FP32 (relative error ~1e-7,
-    over hundreds of steps): bar 1e-4 relative, still orders of magnitude
-    below what an error in S or in the elimination produces."""
+    the oracle's drift on the same cells, per element (floor 1e-13).  The
+    reduced precisions solve each Newton correction in FP32: their bar is
+    fp32_drift_bar (FP32 rounding of the equilibrated solve, summed over the
+    cell's Newton iterations), orders of magnitude below what an error in S
+    or in the elimination produces."""
     d, k, y0, t_end, ref, _ = small_case if case == "stiff" else moderate_case
     y, stats, code = run_gpu(torch, B, d, k, y0, t_end, precision=precision)
     assert code == B.SM_OK
@@ -181,8 +200,11 @@ def test_conservation_gpu(torch, B, small_case, moderate_case, case, precision):
         assert np.all(drift <= 4.0 * np.maximum(drift_o, 1e-13)), (drift, drift_o)
         assert charge <= 4.0 * max(charge_o, 1e-13), (charge, charge_o)
     else:
-        assert np.all(drift <= 1e-4), drift
-        assert charge <= 1e-4 * tot0[0].max(), charge
+        # per cell: the largest relative drift over the elements, and the charge
+        cell_drift = (np.abs(E[:3] @ y - E[:3] @ y0) / tot0).max(axis=0)
+        bar = fp32_drift_bar(stats)
+        assert np.all(cell_drift <= bar), (cell_drift / bar).max()
+        assert np.all(np.abs(E[3] @ y) <= bar * tot0[0]), charge
 
 
 def test_nan_cell_is_isolated(torch, B):
@@ -210,23 +232,45 @@ def test_max_steps_reported(torch, B):
     assert np.all(stats["status"] == B.CELL_MAXSTEPS) and np.all(stats["steps"] == 5)
 
 
+@pytest.fixture(scope="module")
+def strat_case():
+    """The 32 stiffness-stratified cells of the 16,384-cell workload (470 x
+    6000, T 10-1000 K, n_H 1e2-1e8, A_V 0-20, atomic start, 1e6 yr) with the
+    oracle's stored rtol-1e-10 ('truth') and rtol-1e-6 solutions."""
+    import json
+    import os
+    from tests.golden.make_integrate_truth import STRAT_POOL, case_inputs
+    with open(os.path.join(os.path.dirname(__file__), "golden", "integrate_truth_strat.json")) as fh:
+        ref = json.load(fh)
+    d, k, y0, t_end = case_inputs("strat", STRAT_POOL, ref["cells"])
+    return d, k, y0, t_end, np.array(ref["y"]).T, np.array(ref["y_rtol6"]).T, np.array(ref["steps_rtol6"])
+
+
+def cell_err(y, ref, rtol=1e-6, atol=1e-20):
+    """Per cell: largest |y - ref| in units of the integrator's error weight."""
+    return np.max(np.abs(y - ref) / (rtol * np.abs(ref) + atol), axis=0)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
-def test_large_network_matches_oracle(torch, B, precision):
-    """4 cells of the 470 x 6000 network to 1e6 yr against the stored
-    rtol-1e-10 truth; the bar is the oracle's own rtol-1e-6 distance to it
-    (stored by the same script), doubled for FP64 and quadrupled for mixed."""
-    from tests.golden.make_integrate_truth import case_inputs
-    d, k, y0, t_end = case_inputs("large")
-    truth = load_truth("large")
-    yo = load_truth("large", "y_rtol6")
+def test_large_network_matches_oracle(torch, B, strat_case, precision):
+    """32 stiffness-stratified cells of the 470 x 6000 network (45 to 908
+    oracle steps) to 1e6 yr against the stored rtol-1e-10 truth.  The GPU and
+    the oracle run the same method at rtol 1e-6; their global errors are a
+    few to a few tens of tolerance units.  Per cell, the GPU's error must be
+    within STRAT_FACTOR of the oracle's own rtol-1e-6 error (floor: one
+    tolerance unit), and over the cells the median ratio within 1.5."""
+    d, k, y0, t_end, truth, yo, steps_o = strat_case
     y, stats, code = run_gpu(torch, B, d, k, y0, t_end, precision=precision)
     assert code == B.SM_OK, stats["status"]
-    e_o = weighted_err(yo, truth)
-    e_g = weighted_err(y, truth)
-    factor = 2.0 if precision == "fp64" else 4.0
-    assert e_g <= factor * max(e_o, 1.0), (e_g, e_o)
-    # element totals: the same bars as the conservation test (the oracle's
-    # own drift, from its stored rtol-1e-6 solution, for FP64)
+    e_o = np.maximum(cell_err(yo, truth), 1.0)
+    e_g = cell_err(y, truth)
+    ratio = e_g / e_o
+    assert np.all(ratio <= STRAT_FACTOR[precision]), (ratio.max(), int(ratio.argmax()))
+    assert np.median(ratio) <= 1.5, np.median(ratio)
+    assert np.all(np.abs(stats["steps"] - steps_o) <= 0.25 * steps_o + 10)
+    # element totals: FP64 within 4x the oracle's own drift (its stored
+    # rtol-1e-6 solution), the reduced precisions within the FP32 bound of
+    # the conservation test
     E = on.element_matrix(d).astype(float)
     tot0 = np.abs(E[:3] @ y0)
     drift = (np.abs(E[:3] @ y - E[:3] @ y0) / tot0).max(axis=1)
@@ -234,7 +278,8 @@ def test_large_network_matches_oracle(torch, B, precision):
         drift_o = (np.abs(E[:3] @ yo - E[:3] @ y0) / tot0).max(axis=1)
         assert np.all(drift <= 4.0 * np.maximum(drift_o, 1e-13)), (drift, drift_o)
     else:
-        assert np.all(drift <= 1e-4), drift
+        cell_drift = (np.abs(E[:3] @ y - E[:3] @ y0) / tot0).max(axis=0)
+        assert np.all(cell_drift <= fp32_drift_bar(stats)), (cell_drift / fp32_drift_bar(stats)).max()
 
 
 def test_state_reuse_with_new_end_time(torch, B):
@@ -282,31 +327,33 @@ def test_split_newton_rounds_are_bit_identical(torch, B, precision):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
 @pytest.mark.parametrize("with_factors", [True, False])
-def test_state_save_load_resume(torch, B, with_factors):
+def test_state_save_load_resume(torch, B, with_factors, precision):
     """Stop an integration after 40 attempts, save the state to host memory,
     load it into a new state and finish there: with the Newton factors saved
-    the result is the same bits as an uninterrupted run; without them (every
-    cell refactorises once on resume) it is another rtol-1e-6 solution of the
-    same problem, a few tolerance units away."""
+    (FP64 values, or FP32 values in the reduced precisions) the result is the
+    same bits as an uninterrupted run; without them (every cell refactorises
+    once on resume) it is another rtol-1e-6 solution of the same problem, a
+    few tolerance units away."""
     d = sn.generate(2312, 32, 180)
     C = 40
     T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
     k = ok.rate_coefficients(d, T, nH, Av)
     y0 = sc.atomic_start(d, C)
     t_end = 1e3 * YEAR
-    y_ref, s_ref, code = run_gpu(torch, B, d, k, y0, t_end)
+    y_ref, s_ref, code = run_gpu(torch, B, d, k, y0, t_end, precision=precision)
     assert code == B.SM_OK
     ld = B.pad_ld(C)
     net = B.Network(d, 0)
     kd = dev(torch, k, ld)
-    a = B.State(net, C)
+    a = B.State(net, C, precision=precision)
     a.init(kd, dev(torch, y0, ld), t_end, C)
     a.step(kd, 40)
     assert a.read() > 0                       # interrupted mid-run
     image = a.save(with_factors)
     del a
-    b = B.State(net, C)
+    b = B.State(net, C, precision=precision)
     b.load(image)
     for _ in range(2000):
         b.step(kd, 8)
@@ -325,7 +372,99 @@ def test_state_save_load_resume(torch, B, with_factors):
     else:
         units = np.abs(y - y_ref) / (1e-6 * np.abs(y_ref) + 1e-20)
         assert units.max() <= 100.0, units.max()
-    # an image does not fit a state of another shape
-    c = B.State(net, C + 64)
+    # an image does not fit a state of another shape or precision
+    other = "fp64" if precision != "fp64" else "mixed"
+    with pytest.raises(B.StoichError):
+        B.State(net, C, precision=other).load(image)
+    c = B.State(net, C + 64, precision=precision)
     with pytest.raises(B.StoichError):
         c.load(image)
+
+
+def step_by_step(torch, B, d, k, y0, t_end, record=4000, **opts):
+    """Integrates attempt by attempt (sm_step_bdf with one attempt, then
+    sm_state_read) and returns per cell the accepted states y_0, y_1, ...,
+    and the recorded step log (end times, sizes, orders)."""
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+    net = B.Network(d, 0)
+    st = B.State(net, C, record_steps=record, **opts)
+    kd = dev(torch, k, ld)
+    st.init(kd, dev(torch, y0, ld), t_end, C)
+    ys = [[y0[:, c].copy()] for c in range(C)]
+    prev = np.zeros(C, dtype=np.int64)
+    yd = torch.zeros((d.n_s, ld), dtype=torch.float64, device="cuda")
+    stats = B.stats_tensor(C, "cuda")
+    for _ in range(100000):
+        st.step(kd, 1)
+        running = st.read(yd, stats)
+        s = B.stats_to_numpy(stats)
+        y = yd.cpu().numpy()
+        for c in np.nonzero(s["steps"] != prev)[0]:
+            assert s["steps"][c] == prev[c] + 1          # one attempt accepts at most one step
+            ys[c].append(y[:, c].copy())
+        prev = s["steps"].astype(np.int64)
+        if running == 0:
+            break
+    assert np.all(s["status"] == B.CELL_OK), s["status"]
+    m_max = int(prev.max())
+    tl, hl, ql = (a.cpu().numpy() for a in st.steps_log(m_max, C))
+    return ys, tl, hl, ql, s
+
+
+def replay_errors(d, k, ys, tl, hl, ql, sample=None):
+    """One-step replay: for every (or `sample` evenly spaced) accepted step m
+    of every cell, the oracle solves the step's implicit BDF equation exactly
+    from the GPU's own history y_{m-1}, ..., y_{m-q} with the GPU's recorded
+    t_m, h_m, q_m; returns |y_gpu - y_oracle| / (1e-10 |y_oracle| + 1e-24)
+    per checked step (largest over species)."""
+    S = on.stoichiometry(d)
+    out = []
+    for c in range(len(ys)):
+        N = len(ys[c]) - 1
+        ts = [0.0] + [tl[m - 1, c] for m in range(1, N + 1)]
+        ms = range(1, N + 1) if sample is None else sorted(set(np.linspace(1, N, sample).astype(int)))
+        for m in ms:
+            q = int(ql[m - 1, c])
+            yo = ob.solve_step(d, k[:, c], [ys[c][m - 1 - i] for i in range(q)],
+                               [ts[m - 1 - i] for i in range(q)], ts[m], hl[m - 1, c], S, y_start=ys[c][m])
+            out.append(np.max(np.abs(ys[c][m] - yo) / (1e-10 * np.abs(yo) + 1e-24)))
+    return np.array(out)
+
+
+# Largest one-step replay difference allowed, in units of 1e-10 |y| + 1e-24
+# (1e-10 relative above atol / rtol = 1e-14, where the method's weights are
+# relative; 1e-24 absolute below): FP64 at 1; the reduced precisions, whose
+# last Newton correction is an FP32 solve, at their measured level
+REPLAY_BAR = {"fp64": 1.0, "mixed": 1.0, "tf32": 1.0}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
+def test_step_replay_matches_oracle(torch, B, precision):
+    """The step math, independently of the step-size controller: 8 cells of
+    the 32 x 180 network (T 10-1000 K, n_H 1e2-1e8, A_V 0-20) are integrated
+    to 1e6 yr attempt by attempt with the Newton iteration converged to 1e-6
+    in WRMS units, and every accepted GPU step is compared with the oracle's
+    exact solution of the same BDF equation (same history, t_m, h_m, q_m)."""
+    d = sn.generate(2312, 32, 180)
+    C = 8
+    T, nH, Av = sc.conditions(4998, C, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0))
+    k = ok.rate_coefficients(d, T, nH, Av)
+    y0 = sc.atomic_start(d, C)
+    ys, tl, hl, ql, s = step_by_step(torch, B, d, k, y0, 1e6 * YEAR, precision=precision, newton_tol=1e-6,
+                                     newton_max=8, use_graph=0)
+    err = replay_errors(d, k, ys, tl, hl, ql)
+    assert len(err) == int(s["steps"].sum())
+    assert err.max() <= REPLAY_BAR[precision], (err.max(), np.quantile(err, 0.99))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_replay_large_network(torch, B, strat_case, precision):
+    """The same one-step replay on 4 of the stratified 470 x 6000 cells to
+    1e6 yr, 12 evenly spaced accepted steps per cell."""
+    d, k, y0, t_end = strat_case[:4]
+    sel = [0, 8, 16, 24]
+    ys, tl, hl, ql, s = step_by_step(torch, B, d, k[:, sel], y0[:, sel], t_end, precision=precision,
+                                     newton_tol=1e-6, newton_max=8, use_graph=0)
+    err = replay_errors(d, k[:, sel], ys, tl, hl, ql, sample=12)
+    assert err.max() <= REPLAY_BAR[precision], (err.max(), np.quantile(err, 0.99))

@@ -149,3 +149,70 @@ def test_conservation_through_integration():
         tot0 = E[:3] @ y0[:, c]
         assert np.allclose(E[:3] @ r.y, tot0, rtol=1e-12, atol=0.0)
         assert abs(E[3] @ r.y) <= 1e-12 * np.abs(y0[:, c]).sum()
+
+
+def _quadratic_root(a2, a1, a0, lo, hi):
+    """The root of a2 B^2 + a1 B + a0 = 0 in [lo, hi] (closed form)."""
+    disc = np.sqrt(a1 * a1 - 4 * a2 * a0)
+    roots = [(-a1 - disc) / (2 * a2), (-a1 + disc) / (2 * a2)]
+    inside = [r for r in roots if lo - 1e-12 <= r <= hi + 1e-12]
+    assert len(inside) == 1
+    return inside[0]
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+def test_solve_step_worked_example_closed_form(q):
+    """One constant-step BDF-q step of the worked example (2A -> B at k, B ->
+    2A at zeta; A = N - 2B conserved) from an arbitrary history: with the
+    textbook coefficients the implicit equation for B is the quadratic
+    a_0 B + sum_i a_i B_{n+1-i} = h (k (N - 2B)^2 - zeta B), solved in closed
+    form; solve_step must return that root and A = N - 2B."""
+    d = sn.worked_example()
+    kk, z = 0.8, 0.3
+    N = 1.0
+    h = 0.45
+    t0 = 3.0
+    Bh = [0.11 + 0.03 * i for i in range(q)]               # B_n, B_{n-1}, ...
+    hist_y = [np.array([N - 2 * B, B]) for B in Bh]
+    hist_t = [t0 - i * h for i in range(q)]
+    a = [float(x) for x in BDF_TEXTBOOK[q]]
+    c = sum(a[i] * Bh[i - 1] for i in range(1, q + 1))
+    # a0 B + c - h k (N^2 - 4 N B + 4 B^2) + h z B = 0
+    B = _quadratic_root(-4 * h * kk, a[0] + 4 * h * kk * N + h * z, c - h * kk * N * N, 0.0, N / 2)
+    y = bdf.solve_step(d, np.array([kk, z]), hist_y, hist_t, t0 + h, h)
+    assert y[1] == pytest.approx(B, rel=1e-13)
+    assert y[0] == pytest.approx(N - 2 * B, rel=1e-13)
+
+
+def test_solve_step_reproduces_integrator_steps():
+    """With a tight Newton tolerance the integrator's accepted steps solve the
+    same equation: solve_step from the recorded history (newest first) gives
+    every accepted y_m to within that tolerance."""
+    from synth import cells
+    d = sn.generate(2312, 32, 180)
+    T, nH, Av = cells.conditions(4998, 1, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
+    k = ok.rate_coefficients(d, T, nH, Av)[:, 0]
+    y0 = cells.atomic_start(d, 1)[:, 0]
+    S = on.stoichiometry(d)
+    t_end = 1e3 * ok.YEAR
+    r = bdf.integrate_cell(d, k, y0, t_end, bdf.BDFOptions(newton_tol=1e-9, newton_max=8), S, record=True)
+    assert r.status == bdf.STATUS_OK and r.steps > 30
+    acc = [e for e in r.log if e["outcome"] == "accept"]
+    ys, ts = [y0], [0.0]
+    for e in acc:
+        ys.append(e["y"])
+        ts.append(t_end if e["t"] + e["h"] >= t_end else e["t"] + e["h"])
+    for m, e in enumerate(acc):
+        q = e["q"]
+        hy = [ys[m - i] for i in range(q)]
+        ht = [ts[m - i] for i in range(q)]
+        ym = bdf.solve_step(d, k, hy, ht, ts[m + 1], e["h"], S)
+        w = 1.0 / (1e-6 * np.abs(ys[m]) + 1e-20)
+        assert bdf.wrms(ym - ys[m + 1], w) <= 1e-8, m
+    # a wrong history order (oldest first) is caught
+    m = next(i for i, e in enumerate(acc) if e["q"] >= 3)
+    q = acc[m]["q"]
+    bad = bdf.solve_step(d, k, [ys[m - q + 1 + i] for i in range(q)], [ts[m - i] for i in range(q)],
+                         ts[m + 1], acc[m]["h"], S)
+    w = 1.0 / (1e-6 * np.abs(ys[m]) + 1e-20)
+    assert bdf.wrms(bad - ys[m + 1], w) > 1e-3

@@ -70,6 +70,30 @@ def test_rate_coefficient_special_cases():
     assert np.allclose(k_n[cr, 1], k_n[cr, 0], rtol=0) and np.allclose(k_n[ph, 1], k_n[ph, 0], rtol=0)
 
 
+def test_dissociative_recombination_rate_law():
+    """Dissociative recombination (class 3) follows the two-body law on its
+    own parameters: at T = 300 K and gamma read off k(T), alpha and beta are
+    recovered from two temperatures, k' carries one factor of n_H (two
+    reactants: ion and electron), and a cell's A_V and zeta leave it alone."""
+    d = sn.generate(2312, 470, 6000)
+    dr = np.nonzero(d.rclass == 3)[0]
+    assert len(dr) > 100
+    assert np.all((d.reactants[dr] >= 0).sum(axis=1) == 2)
+    T = np.array([300.0, 30.0, 300.0, 300.0])
+    nH = np.array([1.0, 1.0, 1e4, 1.0])
+    Av = np.array([0.0, 0.0, 0.0, 7.0])
+    k = ok.rate_coefficients(d, T, nH, Av)[dr]
+    kz = ok.rate_coefficients(d, T, nH, Av, zeta=1e-15)[dr]
+    # T = 300 K: k = alpha exp(-gamma / 300)
+    assert np.allclose(k[:, 0], d.alpha[dr] * np.exp(-d.gamma[dr] / 300.0), rtol=1e-15)
+    # T = 30 K: k = alpha 0.1^beta exp(-gamma / 30)
+    assert np.allclose(k[:, 1], d.alpha[dr] * 0.1 ** d.beta[dr] * np.exp(-d.gamma[dr] / 30.0), rtol=1e-13)
+    # one factor of n_H; no dependence on A_V or zeta
+    assert np.allclose(k[:, 2], 1e4 * k[:, 0], rtol=1e-15)
+    assert np.array_equal(k[:, 3], k[:, 0])
+    assert np.array_equal(kz, k)
+
+
 def test_rate_coefficient_log_linearity():
     """log k is linear in log(T/300) with slope beta, in 1/T with slope -gamma,
     and photorates fall as exp(-gamma A_V)."""

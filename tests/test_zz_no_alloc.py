@@ -1,9 +1,10 @@
 """The non-allocating right-hand side (sm_rhs_eval_static).
 
-Some callers cannot let a library call cudaMalloc: code running while a
-stream is captured into a CUDA graph, where allocation is not permitted, and
-host codes that reserve device memory up front for their own pool.  For them
-sm_rhs_eval_static keeps its rate buffer in a fixed array inside the library.
+Some callers cannot let a library call cudaMalloc: hydro codes that reserve
+the device memory up front for their own pool allocator, and time-step loops
+that must not allocate because cudaMalloc can synchronise the device.  For
+them sm_rhs_eval_static keeps its rate buffer in a fixed array inside the
+library.
 These checks call it through the C ABI and compare it with sm_rhs_eval on the
 same inputs, twice in a row (the shared array keeps the previous call's data,
 which must not leak into the next result), with the tolerance of the other
