@@ -81,7 +81,7 @@ def args_():
     p.add_argument("--precision", default="mixed", choices=["mixed", "tf32", "fp64"])
     p.add_argument("--cells", type=int, default=65536)
     p.add_argument("--t-end-yr", type=float, default=1e6)
-    p.add_argument("--attempts-est", type=int, default=1600,
+    p.add_argument("--attempts-est", type=int, default=1400,
                    help="expected attempts of one integration; slices are attempts-est / steps long")
     p.add_argument("--time-kernel", default="refresh",
                    choices=["refresh", "rhs", "solve", "predict", "finish"])
@@ -569,6 +569,20 @@ def roofline(info, s, kind, precision, kern_ms, kern_n, peaks):
         fp32 = precision != "fp64"
     elif kind == "rhs":
         unit, units, fp32 = info["rhs_flops"], newton, False
+    elif kind == "solve":
+        # per Newton iteration of a cell: the packed factors once, and the
+        # residual / update vectors (y, psi, f, w, wf read, y written)
+        esz = 8 if precision == "fp64" else 4
+        unit = esz * info["lu_packed"] + 8.0 * 6 * info["n_s"]
+        units = newton
+        per_launch_units = units / kern_n
+        ach = unit * per_launch_units / (kern_ms * 1e-3 / kern_n) / 1e9
+        tr = TRAFFIC.get((kind, precision, kernel_source_hash()))
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None if tr is None else tr * per_launch_units,
+                "kernel": "solve (packed factors, warp per cell)", "avg_launch_ms": kern_ms / kern_n,
+                "timed_launches": kern_n, "total_ms": kern_ms, "units_per_launch": per_launch_units,
+                "bytes_per_unit": unit, "unit_name": "cell Newton iteration", "peak_source": peaks["hbm_source"]}
     else:
         return None
     per_launch_units = units / kern_n
@@ -579,7 +593,7 @@ def roofline(info, s, kind, precision, kern_ms, kern_n, peaks):
     return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
             "traffic": None if tr is None else tr * per_launch_units,
             "kernel": f"{kind} ({'FP32' if fp32 else 'FP64'} pipe)", "avg_launch_ms": kern_ms / kern_n,
-            "timed_launches": kern_n, "units_per_launch": per_launch_units,
+            "timed_launches": kern_n, "total_ms": kern_ms, "units_per_launch": per_launch_units,
             "flops_per_unit": unit, "unit_name": "refreshed cell" if kind == "refresh" else "cell RHS",
             "peak_source": peaks["alu_source"]}
 

@@ -103,6 +103,9 @@ typedef struct {
     double rhs_flops;       /* per cell: 2 nnz_S + sum_j order_j                */
     double jac_bytes;       /* per cell: 8 (n_r + n_s + nnz_J)                  */
     double jac_flops;       /* per cell: 2 n_jac_terms + sum_j order_j          */
+    int64_t lu_packed;      /* values per cell of the factors as the integrator's
+                               substitution reads them (sparse head parts + the
+                               dense trailing block, column-major, padded)     */
 } sm_net_info;
 
 /* Build a network on `device` from an explicit description: validates indices

@@ -44,7 +44,8 @@ class NetInfo_c(ct.Structure):
                 ("lu_flops", ct.c_int64), ("lu_head", ct.c_int32), ("max_row_nnz", ct.c_int32),
                 ("fmt", ct.c_int32), ("order", ct.c_int32), ("sell_C", ct.c_int32),
                 ("sell_sigma", ct.c_int32), ("fmt_entries", ct.c_int64), ("rhs_bytes", ct.c_double),
-                ("rhs_flops", ct.c_double), ("jac_bytes", ct.c_double), ("jac_flops", ct.c_double)]
+                ("rhs_flops", ct.c_double), ("jac_bytes", ct.c_double), ("jac_flops", ct.c_double),
+                ("lu_packed", ct.c_int64)]
 
 
 class TuneResult_c(ct.Structure):

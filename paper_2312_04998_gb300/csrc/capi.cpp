@@ -82,6 +82,11 @@ void release_all(sm_net* net) {
   lu.d_u12off.release();
   lu.d_lrhk.release();
   lu.d_srow.release();
+  lu.d_u11ptr.release();
+  lu.d_flev_ptr.release();
+  lu.d_flev.release();
+  lu.d_blev_ptr.release();
+  lu.d_blev.release();
   net->d_jt_slot.release();
   net->d_jdesc.release();
   net->d_jlong.release();

@@ -29,6 +29,13 @@
 namespace {
 
 constexpr int QMAX = 5;  // highest BDF order; the history keeps QMAX + 1 points
+// counters[] entries of the compaction (0..3 belong to the attempt loop and
+// the adjoint)
+constexpr int kCAct = 8;     // slots holding the running cells: [0, counters[kCAct])
+constexpr int kCHoles = 9;   // finished cells below the new boundary
+constexpr int kCRun = 10;    // running cells above it
+constexpr int kCLive = 11;   // running cells counted for the compaction
+constexpr int kCounters = 16;
 constexpr int kCkpt = SM_CHECKPOINT_EVERY;
 enum : int {
   F_NEED_J = 1, F_REJECTED = 2, F_HAS_EPREV = 4, F_NEWTON = 8, F_CONV = 16,
@@ -47,6 +54,12 @@ struct Dev {
   // per-cell vectors [n][ld]; Y is [QMAX+1][n][ld]
   double *Y, *ypred, *y, *psi, *f, *f0, *eprev, *w, *wf;
   int *list, *counters;  // counters[0] = refresh list length, [1] = running cells
+  // compaction of the running cells (states that record no steps): cell
+  // slots are permuted so that running cells occupy slots [0, counters[kCAct])
+  int* slot_cell;        // [ld] slot -> cell of the caller's arrays (and of the packed factors)
+  int compact;           // 1: compaction on
+  double* kslot;         // [n_r][ld] rate coefficients in slot order (compaction on), else null
+  int *holes, *runners;  // [ld] each: the slot pairs of one compaction
   // recording (record > 0): per accepted step m (1-based) at [m-1][ld]; the
   // step history after every kCkpt-th accepted step at checkpoint m / kCkpt
   int record;
@@ -57,6 +70,13 @@ struct Dev {
   void* lu;
   int64_t lu_stride;
   int ldm;
+  // packed factors read by the substitution (see LUSymbolic): per cell
+  // lup_stride values from lup; null when the state keeps dense factors only
+  void* lup;
+  int64_t lup_stride;
+  int lu_cta;   // 1: lu holds one dense working matrix per refresh CTA (not per cell)
+  int p_l11, p_u11, p_dinv, p_l21, p_u12, p_d, ldd, n_flev, n_blev;
+  const int *u11ptr, *flev_ptr, *flev, *blev_ptr, *blev;
   const int *perm, *iperm, *lptr, *lidx, *uptr, *uidx, *lrptr, *lridx, *ucptr, *ucidx, *jp_ptr, *jt_ptr,
       *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk, *srow;
   int n_srow;
@@ -128,7 +148,12 @@ __global__ void init_copy_kernel(Dev d, const double* __restrict__ yin, int64_t 
     V(Y0, d, s, c) = v;
     ok = ok && isfinite(v);
   }
-  for (int j = 0; j < d.n_r; ++j) ok = ok && isfinite(k[(int64_t)j * ldk + c]);
+  for (int j = 0; j < d.n_r; ++j) {
+    const double kv = k[(int64_t)j * ldk + c];
+    ok = ok && isfinite(kv);
+    if (d.kslot) d.kslot[(int64_t)j * d.ld + c] = kv;
+  }
+  d.slot_cell[c] = (int)c;
   d.status[c] = ok ? SM_CELL_RUNNING : SM_CELL_NAN;
   d.flags[c] = ok ? F_NEWTON : 0;  // F_NEWTON selects the cells for f0
   d.t[c] = 0.0;
@@ -151,6 +176,10 @@ __device__ void store_checkpoint(const Dev& d, int64_t c, int kk) {
 
 __global__ void init_finish_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c == 0) {
+    d.counters[kCAct] = (int)d.C;
+    d.counters[kCHoles] = d.counters[kCRun] = d.counters[kCLive] = 0;
+  }
   if (c >= d.C) return;
   if (d.status[c] != SM_CELL_RUNNING) {
     d.flags[c] = 0;
@@ -183,7 +212,7 @@ __global__ void init_finish_kernel(Dev d) {
 // ---------------------------------------------------------------------------
 __global__ void predict_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C) return;
+  if (c >= d.C || (d.compact && c >= d.counters[kCAct])) return;
   int fl = d.flags[c] & ~(F_CONV | F_FAILED | F_REFRESH | F_FINAL | F_NEWTON | F_ATTEMPT);
   if (d.status[c] != SM_CELL_RUNNING) {
     d.flags[c] = fl;
@@ -425,7 +454,9 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
   const int count = d.counters[0];
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t c = d.list[e];
-    T* A = static_cast<T*>(d.lu) + c * d.lu_stride;
+    T* A = static_cast<T*>(d.lu) + (d.lu_cta ? (int64_t)blockIdx.x : c) * d.lu_stride;
+    T* P = d.lup ? static_cast<T*>(d.lup) + (int64_t)d.slot_cell[c] * d.lup_stride : nullptr;
+    T* D = P ? P + d.p_d : nullptr;   // packed tail block, column-major
     const double gamma = d.gam[c];
     // zero the dense trailing block and the head's pattern entries
     for (int r = warp; r < nt; r += nwarps) {
@@ -707,6 +738,26 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         __syncthreads();
       }
     }
+    // the head's factors are final: copy them into the packed layout of the
+    // substitution (L11, U11, inverse pivots, L21, U12)
+    if (P) {
+      __syncthreads();
+      for (int i = warp; i < h; i += nwarps) {
+        const T* Ai = A + (int64_t)i * ldm;
+        for (int q = __ldg(d.lrptr + i) + lane; q < __ldg(d.lrptr + i + 1); q += 32)
+          P[d.p_l11 + q] = Ai[__ldg(d.lridx + q)];
+        const int u0 = __ldg(d.uptr + i), o11 = __ldg(d.u11ptr + i), n11 = __ldg(d.u11ptr + i + 1) - o11;
+        for (int q = lane; q < n11; q += 32) P[d.p_u11 + o11 + q] = Ai[__ldg(d.uidx + u0 + q)];
+        const int q12 = __ldg(d.uoff + i * np1), o12 = __ldg(d.u12off + i), n12 = __ldg(d.u12off + i + 1) - o12;
+        for (int q = lane; q < n12; q += 32) P[d.p_u12 + o12 + q] = Ai[__ldg(d.uidx + q12 + q)];
+        if (lane == 0) P[d.p_dinv + i] = Ai[i];
+      }
+      for (int i = h + warp; i < n; i += nwarps) {
+        const T* Ai = A + (int64_t)i * ldm;
+        const int p0 = __ldg(d.lrptr + i), o = __ldg(d.lrhoff + i - h), cnt = __ldg(d.lrhead + i - h);
+        for (int q = lane; q < cnt; q += 32) P[d.p_l21 + o + q] = Ai[__ldg(d.lridx + p0 + q)];
+      }
+    }
     // ---- phase C: dense trailing block, blocked right-looking LU
     for (int pb = 0; pb * kNB < nt; ++pb) {
       const int p0 = h + pb * kNB;
@@ -774,8 +825,14 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         }
         __syncthreads();
       }
-      for (int a = warp; a < m; a += nwarps)
-        if (lane < w) A[(int64_t)(p0 + a) * ldm + p0 + lane] = Pt[lane * pitch + a];
+      if (D) {
+        // the panel's columns (diagonal block and L below it) are final
+        for (int b = warp; b < w; b += nwarps)
+          for (int a = lane; a < m; a += 32) D[(int64_t)(p0 - h + b) * d.ldd + (p0 - h + a)] = Pt[b * pitch + a];
+      } else {
+        for (int a = warp; a < m; a += nwarps)
+          if (lane < w) A[(int64_t)(p0 + a) * ldm + p0 + lane] = Pt[lane * pitch + a];
+      }
       if (r > 0) {
         const int rp = round_up(r, 4);
         for (int a = warp; a < w; a += nwarps)
@@ -803,8 +860,16 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
             }
         }
         __syncthreads();
-        for (int a = warp; a < w; a += nwarps)
-          for (int b = lane; b < r; b += 32) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * upitch + b];
+        if (D) {
+          // the panel's U rows are final: column b of the block, rows p0..p0+w
+          for (int e = tid; e < r * 32; e += nthr) {
+            const int b = e >> 5, a = e & 31;
+            if (a < w) D[(int64_t)(p0 - h + w + b) * d.ldd + (p0 - h + a)] = U[a * upitch + b];
+          }
+        } else {
+          for (int a = warp; a < w; a += nwarps)
+            for (int b = lane; b < r; b += 32) A[(int64_t)(p0 + a) * ldm + p0 + w + b] = U[a * upitch + b];
+        }
         // A22 -= L21 U12; L21 column kk is Pt[kk * pitch + w + i]
         bool done = false;
         if constexpr (sizeof(T) == 4) {
@@ -1029,16 +1094,138 @@ __device__ void lu_substitute(const Dev& d, const T* __restrict__ A, T* x, int l
   }
 }
 
+// Substitution with the packed factors of one cell (warp per cell, x in
+// shared memory).  The sparse head is resolved level by level (every row of a
+// level at once, a lane per row), the L21 / U12 couplings a lane per row, and
+// the dense tail block, stored column-major, by 32-column blocks: the
+// block's 32 x 32 diagonal part with warp shuffles, then its columns applied
+// to all remaining rows at once (right-looking), so every factor load is a
+// coalesced 128-byte column segment and the loads of a block do not wait on
+// one another.
+template <class T>
+__device__ void lu_substitute_packed(const Dev& d, const T* __restrict__ P, T* x, int lane) {
+  const int n = d.n, h = d.head, nt = n - h, ldd = d.ldd;
+  const int np1 = (nt + 31) / 32 + 1;
+  T* xt = x + h;
+  const T* __restrict__ D = P + d.p_d;
+  // forward: L11 by levels
+  for (int l = 0; l < d.n_flev; ++l) {
+    const int r1 = __ldg(d.flev_ptr + l + 1);
+    for (int q = __ldg(d.flev_ptr + l) + lane; q < r1; q += 32) {
+      const int i = __ldg(d.flev + q);
+      T s = T(0);
+      for (int p = __ldg(d.lrptr + i); p < __ldg(d.lrptr + i + 1); ++p) s += P[d.p_l11 + p] * x[__ldg(d.lridx + p)];
+      x[i] -= s;
+    }
+    __syncwarp();
+  }
+  // forward: L21 (tail rows, head columns)
+  for (int i = lane; i < nt; i += 32) {
+    const int cnt = __ldg(d.lrhead + i);
+    if (cnt == 0) continue;
+    const int p0 = __ldg(d.lrptr + h + i), o = d.p_l21 + __ldg(d.lrhoff + i);
+    T s = T(0);
+    for (int q = 0; q < cnt; ++q) s += P[o + q] * x[__ldg(d.lridx + p0 + q)];
+    xt[i] -= s;
+  }
+  __syncwarp();
+  // forward: dense tail, unit lower triangle
+  constexpr int kR = 11;   // row chunks of 32 per pass over a block's columns
+  for (int r0 = 0; r0 < nt; r0 += 32) {
+    const int w = min(32, nt - r0);
+    T lcol[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) lcol[k] = (k < w && lane < w && k < lane) ? D[(int64_t)(r0 + k) * ldd + r0 + lane] : T(0);
+    T xi = lane < w ? xt[r0 + lane] : T(0);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const T xk = __shfl_sync(0xffffffffu, xi, k);
+      if (lane > k) xi -= lcol[k] * xk;
+    }
+    if (lane < w) xt[r0 + lane] = xi;
+    // rows below: x_r -= sum_k L(r, r0 + k) x_{r0+k}
+    for (int rb = r0 + 32; rb < nt; rb += 32 * kR) {
+      T acc[kR];
+#pragma unroll
+      for (int t = 0; t < kR; ++t) acc[t] = T(0);
+      for (int k = 0; k < w; ++k) {
+        const T xk = __shfl_sync(0xffffffffu, xi, k);
+        const T* col = D + (int64_t)(r0 + k) * ldd + rb + lane;
+#pragma unroll
+        for (int t = 0; t < kR; ++t)
+          if (rb + 32 * t + lane < nt) acc[t] += col[32 * t] * xk;
+      }
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (rb + 32 * t + lane < nt) xt[rb + 32 * t + lane] -= acc[t];
+    }
+    __syncwarp();
+  }
+  // backward: dense tail, upper triangle with inverse pivots, last block first
+  for (int r0 = (nt - 1) / 32 * 32; r0 >= 0; r0 -= 32) {
+    const int w = min(32, nt - r0);
+    T ucol[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) ucol[k] = (k < w && lane < w && k >= lane) ? D[(int64_t)(r0 + k) * ldd + r0 + lane] : T(0);
+    T xi = lane < w ? xt[r0 + lane] : T(0);
+#pragma unroll
+    for (int k = 31; k >= 0; --k) {
+      if (k < w) {
+        if (lane == k) xi *= ucol[k];   // inverse pivot
+        const T xk = __shfl_sync(0xffffffffu, xi, k);
+        if (lane < k) xi -= ucol[k] * xk;
+      }
+    }
+    if (lane < w) xt[r0 + lane] = xi;
+    // rows above: x_r -= sum_k U(r, r0 + k) x_{r0+k}
+    for (int ra = 0; ra < r0; ra += 32 * kR) {
+      T acc[kR];
+#pragma unroll
+      for (int t = 0; t < kR; ++t) acc[t] = T(0);
+      for (int k = 0; k < w; ++k) {
+        const T xk = __shfl_sync(0xffffffffu, xi, k);
+        const T* col = D + (int64_t)(r0 + k) * ldd + ra + lane;
+#pragma unroll
+        for (int t = 0; t < kR; ++t)
+          if (ra + 32 * t + lane < r0) acc[t] += col[32 * t] * xk;
+      }
+#pragma unroll
+      for (int t = 0; t < kR; ++t)
+        if (ra + 32 * t + lane < r0) xt[ra + 32 * t + lane] -= acc[t];
+    }
+    __syncwarp();
+  }
+  // backward: U12 (head rows, tail columns)
+  for (int i = lane; i < h; i += 32) {
+    const int o = __ldg(d.u12off + i), cnt = __ldg(d.u12off + i + 1) - o, q0 = __ldg(d.uoff + i * np1);
+    T s = T(0);
+    for (int q = 0; q < cnt; ++q) s += P[d.p_u12 + o + q] * x[__ldg(d.uidx + q0 + q)];
+    x[i] -= s;
+  }
+  __syncwarp();
+  // backward: U11 by levels, then the inverse pivot
+  for (int l = 0; l < d.n_blev; ++l) {
+    const int r1 = __ldg(d.blev_ptr + l + 1);
+    for (int q = __ldg(d.blev_ptr + l) + lane; q < r1; q += 32) {
+      const int i = __ldg(d.blev + q);
+      const int o = __ldg(d.u11ptr + i), cnt = __ldg(d.u11ptr + i + 1) - o, u0 = __ldg(d.uptr + i);
+      T s = T(0);
+      for (int e = 0; e < cnt; ++e) s += P[d.p_u11 + o + e] * x[__ldg(d.uidx + u0 + e)];
+      x[i] = (x[i] - s) * P[d.p_dinv + i];
+    }
+    __syncwarp();
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, int need, int want) {
   extern __shared__ unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int64_t c = (int64_t)blockIdx.x * kSolveWarps + wi;
-  if (c >= d.C) return;
+  if (c >= d.C || (d.compact && c >= d.counters[kCAct])) return;
   if ((d.flags[c] & need) != want) return;   // cells in Newton (and, in replays, on this factor set)
   const int n = d.n, xs = (n + 3) / 4 * 4;
   T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)wi * xs;
-  const T* A = static_cast<const T*>(d.lu) + c * d.lu_stride;
   const double a0 = d.alpha[c], h = d.h[c];
   const double inv_a0 = 1.0 / a0;
   for (int s = lane; s < n; s += 32) {
@@ -1048,7 +1235,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, i
     x[__ldg(d.iperm + s)] = T(b);
   }
   __syncwarp();
-  lu_substitute<T>(d, A, x, lane);
+  if (d.lup) lu_substitute_packed<T>(d, static_cast<const T*>(d.lup) + (int64_t)d.slot_cell[c] * d.lup_stride, x, lane);
+  else lu_substitute<T>(d, static_cast<const T*>(d.lu) + c * d.lu_stride, x, lane);
   const double gamma = d.gam[c], gJ = d.gam_J[c];
   const double scale = gamma != gJ ? 2.0 / (1.0 + gamma / gJ) : 1.0;
   double acc = 0.0;
@@ -1089,7 +1277,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, i
 // ---------------------------------------------------------------------------
 __global__ void finish_kernel(Dev d) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C) return;
+  if (c >= d.C || (d.compact && c >= d.counters[kCAct])) return;
   int fl = d.flags[c];
   if (!(fl & F_ATTEMPT)) return;
   fl &= ~F_ATTEMPT;
@@ -1242,8 +1430,9 @@ __global__ void finish_kernel(Dev d) {
 __global__ void read_kernel(Dev d, double* __restrict__ yout, int64_t ldu, sm_cell_stats* __restrict__ st) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.C) return;
+  const int64_t oc = d.slot_cell[c];   // the caller's cell held in slot c
   if (yout)
-    for (int s = 0; s < d.n; ++s) yout[(int64_t)s * ldu + c] = Yh(d, 0)[(int64_t)s * d.ld + c];
+    for (int s = 0; s < d.n; ++s) yout[(int64_t)s * ldu + oc] = Yh(d, 0)[(int64_t)s * d.ld + c];
   if (st) {
     sm_cell_stats r;
     r.status = d.status[c];
@@ -1256,7 +1445,7 @@ __global__ void read_kernel(Dev d, double* __restrict__ yout, int64_t ldu, sm_ce
     r.pad = 0;
     r.t = d.t[c];
     r.h = d.h[c];
-    st[c] = r;
+    st[oc] = r;
   }
 }
 
@@ -1275,6 +1464,86 @@ __global__ void count_running_kernel(Dev d) {
   const int s = d.status[c];
   if (s == SM_CELL_RUNNING) atomicAdd(&d.counters[1], 1);
   else if (s != SM_CELL_OK) atomicAdd(&d.counters[2], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Compaction of the running cells.  Cells finish after very different numbers
+// of steps (a few dozen to over a thousand), and every kernel of an attempt
+// works on whole warps or blocks of consecutive slots, so the finished cells
+// scattered among the running ones cost as much as running ones.  After a
+// group of attempts, once an eighth of the running range has finished, the
+// finished slots below the new boundary (the number of running cells) swap
+// their contents with the running slots above it; the two sets are disjoint,
+// so the swaps need no ordering.  A slot's contents are its per-cell scalars
+// (slot_cell included), its vectors and its rate coefficients; the packed
+// factors stay where they are and are found through slot_cell.  Per-cell results do not
+// depend on the slot, so compaction changes no result.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool compaction_due(int ca, int cn) { return ca - cn >= max(256, ca / 8); }
+
+__global__ void compact_count_kernel(Dev d) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C || c >= d.counters[kCAct]) return;
+  if (d.status[c] == SM_CELL_RUNNING) atomicAdd(&d.counters[kCLive], 1);
+}
+
+__global__ void compact_list_kernel(Dev d) {
+  const int ca = d.counters[kCAct], cn = d.counters[kCLive];
+  if (!compaction_due(ca, cn)) return;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C || c >= ca) return;
+  const bool run = d.status[c] == SM_CELL_RUNNING;
+  if (c < cn && !run) d.holes[atomicAdd(&d.counters[kCHoles], 1)] = (int)c;
+  else if (c >= cn && run) d.runners[atomicAdd(&d.counters[kCRun], 1)] = (int)c;
+}
+
+template <class U>
+__device__ __forceinline__ void swap_rows(U* base, int rows, int64_t ld, int64_t a, int64_t b, int t, int nt) {
+  for (int r = t; r < rows; r += nt) {
+    U* p = base + (int64_t)r * ld;
+    const U va = p[a], vb = p[b];
+    p[a] = vb;
+    p[b] = va;
+  }
+}
+
+__global__ void __launch_bounds__(256) compact_swap_kernel(Dev d) {
+  const int np = min(d.counters[kCHoles], d.counters[kCRun]);
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const int64_t a = d.holes[p], b = d.runners[p];
+    // per-cell scalars: the double rows t .. alpha[QMAX] and the int rows
+    // q .. slot_cell are contiguous with stride ld (see sm_state_create)
+    swap_rows(d.t, 6 + 2 * (QMAX + 1), d.ld, a, b, threadIdx.x, blockDim.x);
+    swap_rows(d.q, 15, d.ld, a, b, threadIdx.x, blockDim.x);
+    // history and working vectors: Y[QMAX + 1], ypred, y, psi, f, f0, eprev, w, wf
+    swap_rows(d.Y, (QMAX + 1 + 8) * d.n, d.ld, a, b, threadIdx.x, blockDim.x);
+    swap_rows(d.kslot, d.n_r, d.ld, a, b, threadIdx.x, blockDim.x);
+  }
+}
+
+__global__ void compact_commit_kernel(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int ca = d.counters[kCAct], cn = d.counters[kCLive];
+    if (compaction_due(ca, cn)) d.counters[kCAct] = cn;
+    d.counters[kCHoles] = d.counters[kCRun] = d.counters[kCLive] = 0;
+  }
+}
+
+// After a state is loaded: every slot counts as possibly running.
+__global__ void set_active_kernel(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    d.counters[kCAct] = (int)d.C;
+    d.counters[kCHoles] = d.counters[kCRun] = d.counters[kCLive] = 0;
+  }
+}
+
+// Rate coefficients in slot order from the caller's array (after a state
+// was loaded, or when sm_step_bdf gets another k than the integration began with).
+__global__ void kslot_gather_kernel(Dev d, const double* __restrict__ k, int64_t ldk) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.C) return;
+  const int64_t oc = d.slot_cell[c];
+  for (int j = 0; j < d.n_r; ++j) d.kslot[(int64_t)j * d.ld + c] = k[(int64_t)j * ldk + oc];
 }
 
 // ---------------------------------------------------------------------------
@@ -1618,7 +1887,8 @@ struct sm_state {
   int64_t cap = 0, C = 0, ld = 0;
   double t_end = 0.0;
   Dev d{};
-  DevArray scal_d, scal_i, vec, lu, list, counters, scratch, rec_d, rec_i;
+  DevArray scal_d, scal_i, vec, lu, lup, list, counters, scratch, rec_d, rec_i, kslot, cpt;
+  const double* kslot_src = nullptr;   // the caller's k the slot-ordered copy was taken from
   DevArray adj_d, adj_i, adj_lu;   // sm_adjoint workspace, grown on demand
   cudaStream_t s = nullptr, s2 = nullptr;          // s2: second half of the Newton rounds
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
@@ -1688,6 +1958,9 @@ void free_state(sm_state* st) {
   st->scal_i.release();
   st->vec.release();
   st->lu.release();
+  st->lup.release();
+  st->kslot.release();
+  st->cpt.release();
   st->list.release();
   st->counters.release();
   st->scratch.release();
@@ -1759,6 +2032,10 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   predict_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_PREDICT, false, s)) != SM_OK) return r;
   if ((r = time_mark(st, SM_TIME_REFRESH, true, s)) != SM_OK) return r;
+  if (d.kslot) {
+    k = d.kslot;   // the rate coefficients in slot order
+    ldk = d.ld;
+  }
   refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(d, k, ldk, st->plan);
   if ((r = time_mark(st, SM_TIME_REFRESH, false, s)) != SM_OK) return r;
   const size_t smem = sizeof(T) * (size_t)kSolveWarps * ((d.n + 3) / 4 * 4);
@@ -1766,7 +2043,8 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   // are split into two halves whose rounds run on two streams: the RHS
   // (FP64-pipe bound) of one half overlaps the substitution (bandwidth
   // bound) of the other.
-  const bool split = st->opts.timing_kind != SM_TIME_RHS && st->opts.timing_kind != SM_TIME_SOLVE &&
+  // (not with compaction: the running cells are then all in the first half)
+  const bool split = !d.compact && st->opts.timing_kind != SM_TIME_RHS && st->opts.timing_kind != SM_TIME_SOLVE &&
                      d.C >= 2 * kSplitMin;
   const int64_t ch = split ? (d.C / 2 + 31) / 32 * 32 : d.C;
   if (split) {
@@ -1777,11 +2055,10 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
     const int64_t c0 = half * ch, cn = split ? (half ? d.C - ch : ch) : d.C;
     cudaStream_t hs = half ? st->s2 : s;
     Dev dh = shift_cells(d, c0, cn);
-    dh.lu = static_cast<T*>(d.lu) + c0 * d.lu_stride;
     for (int m = 0; m < d.newton_max; ++m) {
       if ((r = time_mark(st, SM_TIME_RHS, true, hs)) != SM_OK) return r;
       r = launch_rhs_masked(net, cn, k + c0, ldk, dh.y, dh.f, d.ld, st->scratch.as<double>() + c0, d.ld,
-                            dh.flags, F_NEWTON, hs);
+                            dh.flags, F_NEWTON, d.compact ? d.counters + kCAct : nullptr, hs);
       if (r != SM_OK) return r;
       if ((r = time_mark(st, SM_TIME_RHS, false, hs)) != SM_OK) return r;
       if ((r = time_mark(st, SM_TIME_SOLVE, true, hs)) != SM_OK) return r;
@@ -1807,6 +2084,15 @@ sm_status enqueue_group(sm_state* st, const double* k, int64_t ldk, int attempts
     sm_status r = st->opts.precision != SM_PREC_FP64 ? enqueue_attempt<float>(st, k, ldk, s)
                                                       : enqueue_attempt<double>(st, k, ldk, s);
     if (r != SM_OK) return r;
+  }
+  const Dev& d = st->d;
+  if (d.compact && attempts > 0) {
+    compact_count_kernel<<<blocks(d.C, 256), 256, 0, s>>>(d);
+    compact_list_kernel<<<blocks(d.C, 256), 256, 0, s>>>(d);
+    compact_swap_kernel<<<1024, 256, 0, s>>>(d);
+    compact_commit_kernel<<<1, 32, 0, s>>>(d);
+    SM_TRY_CUDA(cudaGetLastError());
+    st->launches += 4;
   }
   return SM_OK;
 }
@@ -1904,7 +2190,7 @@ Dev shift_cells(const Dev& d0, int64_t c0, int64_t Cc) {
   };
   sh(d.t); sh(d.h); sh(d.gam); sh(d.gam_J); sh(d.crate); sh(d.dprev); sh(d.tn); sh(d.alpha);
   sh(d.q); sh(d.nh); sh(d.n_at_q); sh(d.j_age); sh(d.flags); sh(d.crej); sh(d.ccf); sh(d.status);
-  sh(d.m_it); sh(d.steps); sh(d.rejects); sh(d.conv_fails); sh(d.newton_iters); sh(d.jac_evals);
+  sh(d.m_it); sh(d.steps); sh(d.rejects); sh(d.conv_fails); sh(d.newton_iters); sh(d.jac_evals); sh(d.slot_cell);
   sh(d.Y); sh(d.ypred); sh(d.y); sh(d.psi); sh(d.f); sh(d.f0); sh(d.eprev); sh(d.w); sh(d.wf);
   sh(d.log_t); sh(d.log_h); sh(d.log_q); sh(d.ck_Y); sh(d.ck_t); sh(d.ck_nh);
   return d;
@@ -1919,6 +2205,8 @@ sm_status adj_prepare(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const d
   const int n = st->d.n, n_r = st->d.n_r;
   cudaStream_t s = st->s;
   Dev dd = shift_cells(st->d, c0, Cp);
+  dd.lup = nullptr;   // the replay factorises into dense per-cell storage
+  dd.lu_cta = 0;
   dd.mixed = 0;
   dd.newton_tol = kReplayTol;
   dd.newton_max = kReplayIters;
@@ -2009,7 +2297,7 @@ sm_status adjoint_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const 
         }
         if ((r = refresh_at(j, need)) != SM_OK) return r;
         for (int it = 0; it < kReplayIters; ++it) {
-          r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
+          r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, nullptr, s);
           if (r != SM_OK) return r;
           if (j > 0 && attempt == 0) {
             solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(d_old, need, F_NEWTON);
@@ -2071,7 +2359,7 @@ sm_status replay_pass(sm_state* st, int64_t c0, int64_t Cp, int64_t lda, const d
       refresh_kernel<double><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(dd, kp, ldk, st->plan);
       st->launches += 2;
       for (int it = 0; it < kReplayIters; ++it) {
-        r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, s);
+        r = launch_rhs_masked(net, Cp, kp, ldk, dd.y, dd.f, dd.ld, scratch, dd.ld, dd.flags, F_NEWTON, nullptr, s);
         if (r != SM_OK) return r;
         solve_update_kernel<double><<<blocks(Cp, kSolveWarps), 32 * kSolveWarps, solve_smem, s>>>(dd, F_NEWTON, F_NEWTON);
         st->launches += 3;
@@ -2160,16 +2448,25 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     return e;
   };
   const int n_dscal = 6 + 2 * (QMAX + 1);   // t h gam gam_J crate dprev | tn[6] alpha[6]
-  const int n_iscal = 14;
+  const int n_iscal = 15;                   // q nh n_at_q j_age flags crej ccf status m_it steps rejects
+                                            // conv_fails newton_iters jac_evals slot_cell
   const int n_vec = (QMAX + 1) + 8;         // Y[6] ypred y psi f f0 eprev w wf
   if ((r = st->scal_d.ensure(sizeof(double) * n_dscal * ld)) != SM_OK) return fail(r);
   if ((r = st->scal_i.ensure(sizeof(int) * n_iscal * ld)) != SM_OK) return fail(r);
   if ((r = st->vec.ensure(sizeof(double) * (size_t)n_vec * n * ld)) != SM_OK) return fail(r);
   const size_t esz = d.mixed ? sizeof(float) : sizeof(double);
   d.lu_stride = (int64_t)n * lu.ld;
-  if ((r = st->lu.ensure(esz * (size_t)d.lu_stride * C)) != SM_OK) return fail(r);
+  d.lup_stride = lu.p_size;
+  if ((r = st->lup.ensure(esz * (size_t)d.lup_stride * C)) != SM_OK) return fail(r);
   if ((r = st->list.ensure(sizeof(int) * ld)) != SM_OK) return fail(r);
-  if ((r = st->counters.ensure(sizeof(int) * 4)) != SM_OK) return fail(r);
+  if ((r = st->counters.ensure(sizeof(int) * kCounters)) != SM_OK) return fail(r);
+  // compaction of running cells in states that record no steps (the
+  // adjoint's records are indexed by cell)
+  d.compact = o.record_steps > 0 ? 0 : 1;
+  if (d.compact) {
+    if ((r = st->kslot.ensure(sizeof(double) * (size_t)net->n_r * ld)) != SM_OK) return fail(r);
+    if ((r = st->cpt.ensure(sizeof(int) * 2 * (size_t)ld)) != SM_OK) return fail(r);
+  }
   if ((r = st->scratch.ensure(sizeof(double) * (size_t)net->n_r * ld)) != SM_OK) return fail(r);
   double* ds = st->scal_d.as<double>();
   d.t = ds; d.h = ds + ld; d.gam = ds + 2 * ld; d.gam_J = ds + 3 * ld; d.crate = ds + 4 * ld;
@@ -2178,14 +2475,23 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.q = is; d.nh = is + ld; d.n_at_q = is + 2 * ld; d.j_age = is + 3 * ld; d.flags = is + 4 * ld;
   d.crej = is + 5 * ld; d.ccf = is + 6 * ld; d.status = is + 7 * ld; d.m_it = is + 8 * ld;
   d.steps = is + 9 * ld; d.rejects = is + 10 * ld; d.conv_fails = is + 11 * ld;
-  d.newton_iters = is + 12 * ld; d.jac_evals = is + 13 * ld;
+  d.newton_iters = is + 12 * ld; d.jac_evals = is + 13 * ld; d.slot_cell = is + 14 * ld;
   double* v = st->vec.as<double>();
   const int64_t vs = (int64_t)n * ld;
   d.Y = v; d.ypred = v + (QMAX + 1) * vs; d.y = d.ypred + vs; d.psi = d.y + vs; d.f = d.psi + vs;
   d.f0 = d.f + vs; d.eprev = d.f0 + vs; d.w = d.eprev + vs; d.wf = d.w + vs;
   d.list = st->list.as<int>();
   d.counters = st->counters.as<int>();
+  d.kslot = d.compact ? st->kslot.as<double>() : nullptr;
+  d.holes = d.compact ? st->cpt.as<int>() : nullptr;
+  d.runners = d.compact ? st->cpt.as<int>() + ld : nullptr;
   d.lu = st->lu.p;
+  d.lup = st->lup.p;
+  d.p_l11 = lu.p_l11; d.p_u11 = lu.p_u11; d.p_dinv = lu.p_dinv; d.p_l21 = lu.p_l21; d.p_u12 = lu.p_u12;
+  d.p_d = lu.p_d; d.ldd = lu.ldd;
+  d.n_flev = (int)lu.flev_ptr.size() - 1; d.n_blev = (int)lu.blev_ptr.size() - 1;
+  d.u11ptr = lu.d_u11ptr.as<int>(); d.flev_ptr = lu.d_flev_ptr.as<int>(); d.flev = lu.d_flev.as<int>();
+  d.blev_ptr = lu.d_blev_ptr.as<int>(); d.blev = lu.d_blev.as<int>();
   d.perm = lu.d_perm.as<int>(); d.iperm = lu.d_iperm.as<int>();
   d.lptr = lu.d_lptr.as<int>(); d.lidx = lu.d_lidx.as<int>();
   d.uptr = lu.d_uptr.as<int>(); d.uidx = lu.d_uidx.as<int>();
@@ -2224,7 +2530,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   if (cudaStreamCreateWithFlags(&st->s2, cudaStreamNonBlocking) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
   if (cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming) != cudaSuccess) return fail(SM_ECUDA);
-  if (cudaMallocHost(&st->h_counters, 4 * sizeof(int)) != cudaSuccess) return fail(SM_ENOMEM);
+  if (cudaMallocHost(&st->h_counters, kCounters * sizeof(int)) != cudaSuccess) return fail(SM_ENOMEM);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device);
   int smem_max = 0;
@@ -2286,6 +2592,11 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<double>, kRefreshThreads, rsm);
   }
   st->refresh_ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  // dense working matrices of the refresh: one per refresh CTA, except in
+  // recording states, whose replays keep dense factors per cell
+  d.lu_cta = d.record ? 0 : 1;
+  if ((r = st->lu.ensure(esz * (size_t)d.lu_stride * (d.lu_cta ? st->refresh_ctas : C))) != SM_OK) return fail(r);
+  d.lu = st->lu.p;
   SM_TRY_CUDA(cudaMemset(st->scal_i.p, 0, st->scal_i.bytes));
   *out = st;
   return SM_OK;
@@ -2301,7 +2612,8 @@ sm_status sm_state_free(sm_state* st) {
 
 sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
   if (!st || !bytes) return SM_EINVAL;
-  *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->list.bytes +
+  *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->lup.bytes + st->kslot.bytes +
+           st->cpt.bytes + st->list.bytes +
            st->counters.bytes + st->scratch.bytes + st->rec_d.bytes + st->rec_i.bytes + st->adj_d.bytes + st->adj_i.bytes +
            st->adj_lu.bytes;
   return SM_OK;
@@ -2321,8 +2633,9 @@ sm_status sm_state_init(sm_state* st, int64_t C, const double* d_k, const double
   d.t_end = t_end;
   init_copy_kernel<<<blocks(C, 128), 128, 0, st->s>>>(d, d_y, ld, d_k, ld);
   SM_TRY_CUDA(cudaGetLastError());
+  st->kslot_src = d_k;
   r = launch_rhs_masked(st->net, C, d_k, ld, d.Y, d.f0, d.ld, st->scratch.as<double>(), d.ld, d.flags,
-                        F_NEWTON, st->s);
+                        F_NEWTON, nullptr, st->s);
   if (r != SM_OK) return r;
   init_finish_kernel<<<blocks(C, 128), 128, 0, st->s>>>(d);
   SM_TRY_CUDA(cudaGetLastError());
@@ -2336,6 +2649,12 @@ sm_status sm_step_bdf(sm_state* st, const double* d_k, int64_t ld, int32_t attem
   if (!scope.ok) return SM_ECUDA;
   sm_status r;
   if ((r = join_in(st, stream)) != SM_OK) return r;
+  if (st->d.kslot && st->kslot_src != d_k) {
+    kslot_gather_kernel<<<blocks(st->C, 128), 128, 0, st->s>>>(st->d, d_k, ld);
+    SM_TRY_CUDA(cudaGetLastError());
+    st->launches += 1;
+    st->kslot_src = d_k;
+  }
   if ((r = run_attempts(st, d_k, ld, attempts)) != SM_OK) return r;
   return join_out(st, stream);
 }
@@ -2477,7 +2796,8 @@ void image_sizes(const sm_state* st, int with_factors, uint64_t* b) {
   b[1] = st->scal_i.bytes;
   b[2] = st->vec.bytes;
   b[3] = st->rec_d.bytes + st->rec_i.bytes;
-  b[4] = with_factors ? st->lu.bytes : 0;
+  // the packed factors, and in recording states the dense per-cell ones
+  b[4] = with_factors ? st->lup.bytes + (st->d.lu_cta ? 0 : st->lu.bytes) : 0;
 }
 
 }  // namespace
@@ -2497,7 +2817,7 @@ extern "C" sm_status sm_state_save(sm_state* st, int32_t with_factors, void* hos
   if ((r = join_in(st, stream)) != SM_OK) return r;
   StateImage im{};
   im.magic = kImageMagic;
-  im.version = 1;
+  im.version = 2;
   im.n_s = st->d.n;
   im.n_r = st->d.n_r;
   im.precision = st->opts.precision;
@@ -2524,7 +2844,11 @@ extern "C" sm_status sm_state_save(sm_state* st, int32_t with_factors, void* hos
     SM_TRY_CUDA(cudaMemcpyAsync(dst, st->rec_i.p, st->rec_i.bytes, cudaMemcpyDeviceToHost, st->s));
     dst += st->rec_i.bytes;
   }
-  if (b[4]) SM_TRY_CUDA(cudaMemcpyAsync(dst, st->lu.p, b[4], cudaMemcpyDeviceToHost, st->s));
+  if (b[4]) {
+    SM_TRY_CUDA(cudaMemcpyAsync(dst, st->lup.p, st->lup.bytes, cudaMemcpyDeviceToHost, st->s));
+    if (b[4] > st->lup.bytes)
+      SM_TRY_CUDA(cudaMemcpyAsync(dst + st->lup.bytes, st->lu.p, st->lu.bytes, cudaMemcpyDeviceToHost, st->s));
+  }
   SM_TRY_CUDA(cudaStreamSynchronize(st->s));
   return join_out(st, stream);
 }
@@ -2538,7 +2862,7 @@ extern "C" sm_status sm_state_load(sm_state* st, const void* host, size_t bytes,
   const size_t total = sizeof(StateImage) + b[0] + b[1] + b[2] + b[3] + b[4];
   // the image must come from a state of the same shape: network size,
   // capacity, precision and recording
-  if (im.magic != kImageMagic || im.version != 1 || im.n_s != st->d.n || im.n_r != st->d.n_r ||
+  if (im.magic != kImageMagic || im.version != 2 || im.n_s != st->d.n || im.n_r != st->d.n_r ||
       im.precision != st->opts.precision || im.cap != st->cap || im.ld != st->ld ||
       im.lu_stride != st->d.lu_stride || im.record != st->d.record || im.C < 1 || im.C > st->cap ||
       bytes < total)
@@ -2563,11 +2887,19 @@ extern "C" sm_status sm_state_load(sm_state* st, const void* host, size_t bytes,
     SM_TRY_CUDA(cudaMemcpyAsync(st->rec_i.p, src, st->rec_i.bytes, cudaMemcpyHostToDevice, st->s));
     src += st->rec_i.bytes;
   }
-  if (b[4]) SM_TRY_CUDA(cudaMemcpyAsync(st->lu.p, src, b[4], cudaMemcpyHostToDevice, st->s));
+  if (b[4]) {
+    SM_TRY_CUDA(cudaMemcpyAsync(st->lup.p, src, st->lup.bytes, cudaMemcpyHostToDevice, st->s));
+    if (b[4] > st->lup.bytes)
+      SM_TRY_CUDA(cudaMemcpyAsync(st->lu.p, src + st->lup.bytes, st->lu.bytes, cudaMemcpyHostToDevice, st->s));
+  }
   st->C = im.C;
   st->t_end = im.t_end;
   st->d.C = im.C;
   st->d.t_end = im.t_end;
+  st->kslot_src = nullptr;   // regathered from the next sm_step_bdf's d_k
+  set_active_kernel<<<1, 32, 0, st->s>>>(st->d);
+  SM_TRY_CUDA(cudaGetLastError());
+  st->launches += 1;
   if (!im.with_factors) {
     need_j_kernel<<<blocks(im.C, 128), 128, 0, st->s>>>(st->d);
     SM_TRY_CUDA(cudaGetLastError());

@@ -80,7 +80,22 @@ struct LUSymbolic {
   std::vector<int32_t> uoff;              // per head row k: [n_panels + 1] offsets into its U list where
                                           // the tail columns of each 32-wide panel start
   std::vector<int32_t> jpos;              // per J pattern entry: dense offset p*ld+q
+  // Packed factor layout read by the substitution (per cell, values only,
+  // in the precision of the factors), segment offsets in elements:
+  //   [p_l11, +lrptr[head])   L11: head rows' L entries, order of lrptr/lridx
+  //   [p_u11, +u11ptr[head])  U11: head rows' U entries in head columns
+  //   [p_dinv, +head)         inverse pivots of the head
+  //   [p_l21, +lrhoff[nt])    L21: tail rows' L entries in head columns
+  //   [p_u12, +u12off[head])  U12: head rows' U entries in tail columns
+  //   [p_d, +nt * ldd)        the dense tail block, column-major (L below the
+  //                           diagonal, U above, inverse pivots on it)
+  int32_t p_l11 = 0, p_u11 = 0, p_dinv = 0, p_l21 = 0, p_u12 = 0, p_d = 0, ldd = 0;
+  int64_t p_size = 0;
+  std::vector<int32_t> u11ptr;            // per head row: start of its U11 entries (head + 1)
+  std::vector<int32_t> flev_ptr, flev;    // head rows grouped by forward-substitution level
+  std::vector<int32_t> blev_ptr, blev;    // head rows grouped by backward-substitution level
   int64_t nnz = 0, flops = 0;
+  DevArray d_u11ptr, d_flev_ptr, d_flev, d_blev_ptr, d_blev;
   DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_ucptr, d_ucidx, d_jpos, d_perm, d_iperm,
       d_jrc, d_uoff, d_lrhead, d_lrhoff, d_u12off, d_lrhk, d_srow;
 };
@@ -132,10 +147,11 @@ sm_status launch_rates(const sm_net* net, int64_t C, const double* T, const doub
 sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double* y,
                      double* f, int64_t ld, double* scratch, int64_t ld_scratch, cudaStream_t s);
 // Masked CRS right-hand side for the integrator: cells whose mask word has
-// `bit` set are evaluated; whole thread blocks without such a cell exit.
+// `bit` set are evaluated; whole thread blocks without such a cell exit, and
+// with cact (device, may be null) so do blocks of cells at or past *cact.
 sm_status launch_rhs_masked(const sm_net* net, int64_t C, const double* k, int64_t ldk,
                             const double* y, double* f, int64_t ld, double* scratch, int64_t ldr,
-                            const int* mask, int bit, cudaStream_t s);
+                            const int* mask, int bit, const int* cact, cudaStream_t s);
 // Per-device set-up of the right-hand-side kernels (constant tables); called
 // when a network is uploaded.
 sm_status rhs_prepare_device(int device);

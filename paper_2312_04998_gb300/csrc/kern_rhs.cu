@@ -52,7 +52,8 @@ __device__ __forceinline__ double neg_if(double v, bool neg) {
 __global__ void __launch_bounds__(kRThreads)
 reaction_rate_kernel(int n_r, int64_t C, const int2* __restrict__ reac, const double* __restrict__ k,
                      int64_t ldk, const double* __restrict__ y, int64_t ldy, double* __restrict__ r,
-                     int64_t ldr, const int* __restrict__ mask, int bit) {
+                     int64_t ldr, const int* __restrict__ mask, int bit, const int* __restrict__ cact) {
+  if (cact && (int64_t)blockIdx.x * kRThreads >= *cact) return;   // no running cell in this block
   const int64_t c = (int64_t)blockIdx.x * kRThreads + threadIdx.x;
   const bool act = c < C && (!mask || (mask[c] & bit));
   if (mask && !__syncthreads_or(act)) return;
@@ -86,7 +87,8 @@ __global__ void __launch_bounds__(kCells * kChunks)
 rhs_crs_kernel(int n_s, int64_t C, const int* __restrict__ row_ptr, const uint32_t* __restrict__ ent,
                const int* __restrict__ row_id, const int* __restrict__ chunk_nz,
                const double* __restrict__ r, int64_t ldr, double* __restrict__ f, int64_t ld,
-               const int* __restrict__ mask, int bit) {
+               const int* __restrict__ mask, int bit, const int* __restrict__ cact) {
+  if (cact && (int64_t)blockIdx.x * kCells >= *cact) return;      // no running cell in this block
   __shared__ double part[kChunks][2][kCells];
   __shared__ int carry_row[kChunks];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -245,7 +247,7 @@ sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double
   {
     dim3 grid(groups_r, (unsigned)((net->n_r + kRChunk - 1) / kRChunk));
     reaction_rate_kernel<<<grid, kRThreads, 0, s>>>(net->n_r, C, net->d_reac.as<int2>(), k, ld, y, ld,
-                                                    scratch, ldr, nullptr, 0);
+                                                    scratch, ldr, nullptr, 0, nullptr);
     SM_TRY_CUDA(cudaGetLastError());
   }
   const unsigned groups = (unsigned)((C + kCells - 1) / kCells);
@@ -254,7 +256,7 @@ sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double
     rhs_crs_kernel<<<groups, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
                                                        F.d_packed.as<uint32_t>(), F.d_aux.as<int>(),
                                                        F.d_chunk.as<int>(), scratch, ldr, f, ld,
-                                                       nullptr, 0);
+                                                       nullptr, 0, nullptr);
   } else if (F.fmt == SM_FMT_COO) {
     SM_TRY_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * (size_t)net->n_s * ld, s));
     const int nnz = (int)F.idx.size();
@@ -273,18 +275,18 @@ sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double
 
 sm_status launch_rhs_masked(const sm_net* net, int64_t C, const double* k, int64_t ldk,
                             const double* y, double* f, int64_t ld, double* scratch, int64_t ldr,
-                            const int* mask, int bit, cudaStream_t s) {
+                            const int* mask, int bit, const int* cact, cudaStream_t s) {
   if (C == 0) return SM_OK;
   sm_status st = ensure_coef_table(net->device);
   if (st != SM_OK) return st;
   const Format& F = net->integ;
   dim3 grid((unsigned)((C + kRThreads - 1) / kRThreads), (unsigned)((net->n_r + kRChunk - 1) / kRChunk));
   reaction_rate_kernel<<<grid, kRThreads, 0, s>>>(net->n_r, C, net->d_reac.as<int2>(), k, ldk, y, ld,
-                                                  scratch, ldr, mask, bit);
+                                                  scratch, ldr, mask, bit, cact);
   SM_TRY_CUDA(cudaGetLastError());
   rhs_crs_kernel<<<(unsigned)((C + kCells - 1) / kCells), kCells * kChunks, 0, s>>>(
       net->n_s, C, F.d_ptr.as<int>(), F.d_packed.as<uint32_t>(), F.d_aux.as<int>(), F.d_chunk.as<int>(),
-      scratch, ldr, f, ld, mask, bit);
+      scratch, ldr, f, ld, mask, bit, cact);
   SM_TRY_CUDA(cudaGetLastError());
   return SM_OK;
 }

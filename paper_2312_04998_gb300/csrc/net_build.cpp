@@ -326,6 +326,41 @@ void build_lu_symbolic(sm_net& net) {
     for (int32_t k = 0; k < lu.head; ++k)
       lu.u12off.push_back(lu.u12off.back() + lu.uptr[k + 1] - lu.uoff[(size_t)k * np1]);
   }
+  // packed factor layout of the substitution and the level sets of its
+  // sparse head: a head row's level is one more than the highest level among
+  // the rows its L11 (forward) or U11 (backward) entries refer to, so all
+  // rows of one level can be resolved at once
+  {
+    const int32_t h = lu.head, nt = n - h, np1 = (nt + 31) / 32 + 1;
+    lu.u11ptr.assign(1, 0);
+    for (int32_t k = 0; k < h; ++k) lu.u11ptr.push_back(lu.u11ptr.back() + lu.uoff[(size_t)k * np1] - lu.uptr[k]);
+    auto group = [](const std::vector<int32_t>& lev, std::vector<int32_t>& ptr, std::vector<int32_t>& rows) {
+      int32_t top = 0;
+      for (int32_t v : lev) top = std::max(top, v + 1);
+      ptr.assign(top + 1, 0);
+      for (int32_t v : lev) ++ptr[v + 1];
+      for (int32_t l = 0; l < top; ++l) ptr[l + 1] += ptr[l];
+      rows.assign(lev.size(), 0);
+      std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+      for (int32_t i = 0; i < (int32_t)lev.size(); ++i) rows[fill[lev[i]]++] = i;
+    };
+    std::vector<int32_t> fl(h, 0), bl(h, 0);
+    for (int32_t i = 0; i < h; ++i)
+      for (int32_t p = lu.lrptr[i]; p < lu.lrptr[i + 1]; ++p) fl[i] = std::max(fl[i], fl[lu.lridx[p]] + 1);
+    for (int32_t k = h - 1; k >= 0; --k)
+      for (int32_t p = lu.uptr[k]; p < lu.uoff[(size_t)k * np1]; ++p) bl[k] = std::max(bl[k], bl[lu.uidx[p]] + 1);
+    group(fl, lu.flev_ptr, lu.flev);
+    group(bl, lu.blev_ptr, lu.blev);
+    auto up32 = [](int64_t v) { return (v + 31) / 32 * 32; };
+    lu.p_l11 = 0;
+    lu.p_u11 = (int32_t)up32(lu.p_l11 + (h > 0 ? lu.lrptr[h] : 0));
+    lu.p_dinv = (int32_t)up32(lu.p_u11 + lu.u11ptr[h]);
+    lu.p_l21 = (int32_t)up32(lu.p_dinv + h);
+    lu.p_u12 = (int32_t)up32(lu.p_l21 + lu.lrhoff.back());
+    lu.p_d = (int32_t)up32(lu.p_u12 + lu.u12off.back());
+    lu.ldd = (int32_t)up32(nt);
+    lu.p_size = up32((int64_t)lu.p_d + (int64_t)nt * lu.ldd);
+  }
   lu.jpos.resize(net.jp_col.size());
   lu.jrc.resize(net.jp_col.size());
   for (int32_t i = 0; i < n; ++i)
@@ -434,6 +469,7 @@ sm_status net_build_host(const sm_net_desc* d, sm_net* net) {
   in.rhs_flops = 2.0 * in.nnz_S + (double)sum_order;
   in.jac_bytes = 8.0 * (n_r + n_s + (double)in.nnz_J);
   in.jac_flops = 2.0 * in.n_jac_terms + (double)sum_order;
+  in.lu_packed = net->lu.p_size;
   return SM_OK;
 }
 
@@ -681,6 +717,11 @@ sm_status net_upload(sm_net* net) {
   if ((st = lu.d_u12off.upload(lu.u12off.data(), lu.u12off.size() * 4)) != SM_OK) return st;
   if (!lu.lrhk.empty() && (st = lu.d_lrhk.upload(lu.lrhk.data(), lu.lrhk.size() * 4)) != SM_OK) return st;
   if (!lu.srow.empty() && (st = lu.d_srow.upload(lu.srow.data(), lu.srow.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_u11ptr.upload(lu.u11ptr.data(), lu.u11ptr.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_flev_ptr.upload(lu.flev_ptr.data(), lu.flev_ptr.size() * 4)) != SM_OK) return st;
+  if (!lu.flev.empty() && (st = lu.d_flev.upload(lu.flev.data(), lu.flev.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_blev_ptr.upload(lu.blev_ptr.data(), lu.blev_ptr.size() * 4)) != SM_OK) return st;
+  if (!lu.blev.empty() && (st = lu.d_blev.upload(lu.blev.data(), lu.blev.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_perm.upload(lu.perm.data(), lu.perm.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_iperm.upload(lu.iperm.data(), lu.iperm.size() * 4)) != SM_OK) return st;
   int32_t zero = 0;
