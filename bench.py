@@ -97,6 +97,8 @@ def args_():
                    help="auxiliary measurements start only while the run is younger than this")
     p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe"],
                    help="run one auxiliary measurement alone and print it")
+    p.add_argument("--phases", action="store_true",
+                   help="refresh-kernel cycles per phase over one integration (phase-clock build)")
     return p.parse_args()
 
 
@@ -549,6 +551,36 @@ def adjoint_measurement(B, C, dev):
     return out
 
 
+def phase_profile(B, a, dev):
+    """Refresh-kernel cycles per phase, per refreshed cell, over one whole
+    integration of the first a.cells cells of the headline workload (thread
+    0 of each CTA, between the barriers that end the phases; the phase-clock
+    build of the library)."""
+    import numpy as np
+    import torch
+    from synth.workloads import make
+    d, T, nH, Av, y0 = make(WORKLOAD, cells=a.cells)
+    net = B.Network(d, dev.index or 0)
+    kd, y0d = gpu_inputs(B, net, d, T, nH, Av, y0, dev)
+    st = B.State(net, a.cells, precision=a.precision)
+    stats = B.stats_tensor(a.cells, dev)
+    st.init(kd, y0d, a.t_end_yr * YEAR, a.cells)
+    st.step(kd, 8)
+    torch.cuda.synchronize()
+    B.phase_cycles(dev.index or 0, reset=True)
+    yd = y0d.clone()
+    st.integrate(kd, yd, a.t_end_yr * YEAR, a.cells, stats)
+    torch.cuda.synchronize()
+    cyc = B.phase_cycles(dev.index or 0)
+    cells = max(cyc[15], 1.0)
+    per = cyc[:len(B.PHASE_NAMES)] / cells
+    tot = per.sum()
+    return {"what": "refresh kernel cycles per refreshed cell, by phase (thread 0 of each CTA)",
+            "workload": WORKLOAD, "cells": a.cells, "precision": a.precision, "refreshed_cells": int(cyc[15]),
+            "total_cycles_per_cell": float(tot),
+            "phases": [[nm, float(v), float(v / tot)] for nm, v in zip(B.PHASE_NAMES, per)]}
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2312_04998_gb300", "csrc", "integrate.cu"), "rb") as fh:
@@ -614,6 +646,12 @@ def main():
     __graft_entry__.build()
     from paper_2312_04998_gb300 import binding as B
     from synth.workloads import make
+    if a.phases:
+        from paper_2312_04998_gb300 import build as _bld
+        _bld.build(phase_clocks=True)
+        B.use_phase_build()
+        print(json.dumps(phase_profile(B, a, torch.device("cuda", local))))
+        return
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)

@@ -437,6 +437,16 @@ sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, in
  * device's legacy stream.  SM_EINVAL on a NULL pointer or negative device. */
 sm_status sm_probe_fma(int32_t device, int32_t fp64, double* tflops);
 
+/* Per-phase cycle counters of the Newton-matrix refresh (a diagnostic for
+ * profiling; the library must be built with the phase-clock option, see the
+ * package's build.py, otherwise SM_ENOTSUP).  h_out receives 16 doubles:
+ * slots 0-10 the clock64() cycles summed over all CTAs of `device` for the
+ * phases zero / dR / weights, Jacobian gather and M, sparse head, head
+ * Schur complement, head packing, panel loads, panel LU, U block load, U
+ * block solve, trailing update, epilogue; slot 15 the refreshed cells.
+ * reset = 1 zeroes the counters after reading them. */
+sm_status sm_phase_cycles(int32_t device, double* h_out, int32_t reset);
+
 /* Wait for all work on `stream` and report (and clear) any error a kernel of
  * this network wrote to its device status word. */
 sm_status sm_sync(const sm_net* net, void* stream);

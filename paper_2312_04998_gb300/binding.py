@@ -15,6 +15,9 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libstoich.so")
+# libstoich_phases.so (the phase-clock profiling build) when STOICH_PHASES=1
+if os.environ.get("STOICH_PHASES") == "1":
+    LIB_PATH = os.path.join(_PKG, "libstoich_phases.so")
 
 SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ENOTCONS, SM_ETIMEOUT, SM_EPARTIAL, SM_ENOTSUP, SM_ETOOBIG = range(9)
 STATIC_SCRATCH_DOUBLES = 4194304
@@ -97,6 +100,7 @@ _SIGS = [
                                  ct.c_int64, ct.c_void_p]),
     ("sm_sync", ct.c_int32, [ct.c_void_p, ct.c_void_p]),
     ("sm_probe_fma", ct.c_int32, [ct.c_int32, ct.c_int32, ct.POINTER(ct.c_double)]),
+    ("sm_phase_cycles", ct.c_int32, [ct.c_int32, ct.c_void_p, ct.c_int32]),
     ("sm_opts_default", None, [ct.POINTER(Opts_c)]),
     ("sm_state_create", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.POINTER(Opts_c), ct.POINTER(ct.c_void_p)]),
     ("sm_state_free", ct.c_int32, [ct.c_void_p]),
@@ -447,6 +451,28 @@ def probe_fma(device: int, fp64: bool) -> float:
     v = ct.c_double()
     _check(lib().sm_probe_fma(int(device), int(bool(fp64)), ct.byref(v)), "sm_probe_fma")
     return v.value
+
+
+PHASE_NAMES = ["zero + dR + weights", "Jacobian gather + M", "sparse head (A11, L21, U12)",
+               "head Schur complement", "head packing", "panel loads", "panel LU", "U block load",
+               "U block solve", "trailing update", "epilogue"]
+
+
+def use_phase_build():
+    """Switch this process to libstoich_phases.so (the phase-clock build made
+    by build.build(phase_clocks=True)); call before creating any handle."""
+    global _lib, LIB_PATH
+    LIB_PATH = os.path.join(_PKG, "libstoich_phases.so")
+    _lib = None
+    lib()
+
+
+def phase_cycles(device: int, reset: bool = False) -> np.ndarray:
+    """Refresh-kernel cycles per phase (16 slots, see sm_phase_cycles);
+    needs the phase-clock build (STOICH_PHASES=1)."""
+    out = np.zeros(16)
+    _check(lib().sm_phase_cycles(int(device), out.ctypes.data, int(bool(reset))), "sm_phase_cycles")
+    return out
 
 
 def stats_tensor(C, device):

@@ -43,21 +43,31 @@ def _digest(srcs, extra):
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Compile and link; returns the path of the shared library."""
+PHASE_LIB = os.path.join(PKG, "libstoich_phases.so")
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, phase_clocks: bool = False) -> str:
+    """Compile and link; returns the path of the shared library.  With
+    phase_clocks the refresh kernel's per-phase cycle counters are compiled
+    in (-DSM_PHASE_CLOCKS) and the result is libstoich_phases.so, built in
+    its own folder; the regular library is not touched."""
     nvcc = _nvcc()
     srcs = sources()
     extra = ["-Xptxas", "-v"] if ptxas_v else []
+    if phase_clocks:
+        extra = extra + ["-DSM_PHASE_CLOCKS"]
+    lib_out = PHASE_LIB if phase_clocks else LIB
+    build_dir = BUILD + ("_phases" if phase_clocks else "")
     digest = _digest(srcs, extra)
-    stamp = os.path.join(BUILD, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = os.path.join(build_dir, "stamp")
+    if not force and os.path.exists(lib_out) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == digest:
-                return LIB
-    os.makedirs(BUILD, exist_ok=True)
+                return lib_out
+    os.makedirs(build_dir, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc] + FLAGS + ["-x", "c++", "-c", src, "-o", obj]
@@ -72,15 +82,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for obj, err in results:
             if err.strip():
                 print(f"== {os.path.basename(obj)}\n{err}")
-    tmp = LIB + ".tmp"
+    tmp = lib_out + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_out)
     with open(stamp, "w") as fh:
         fh.write(digest)
-    return LIB
+    return lib_out
 
 
 if __name__ == "__main__":

@@ -83,6 +83,10 @@ void release_all(sm_net* net) {
   lu.d_lrhk.release();
   lu.d_srow.release();
   lu.d_u11ptr.release();
+  lu.d_hop_ptr.release();
+  lu.d_hop.release();
+  lu.d_hop_piv.release();
+  lu.d_hterm.release();
   lu.d_flev_ptr.release();
   lu.d_flev.release();
   lu.d_blev_ptr.release();

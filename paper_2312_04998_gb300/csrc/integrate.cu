@@ -77,6 +77,10 @@ struct Dev {
   int lu_cta;   // 1: lu holds one dense working matrix per refresh CTA (not per cell)
   int p_l11, p_u11, p_dinv, p_l21, p_u12, p_d, ldd, n_flev, n_blev;
   const int *u11ptr, *flev_ptr, *flev, *blev_ptr, *blev;
+  const int *hop_ptr, *hop_piv;     // head program (see LUSymbolic)
+  const int4* hop;
+  const int2* hterm;
+  int n_hlev;
   const int *perm, *iperm, *lptr, *lidx, *uptr, *uidx, *lrptr, *lridx, *ucptr, *ucidx, *jp_ptr, *jt_ptr,
       *jpos, *jrc, *uoff, *lrhead, *lrhoff, *u12off, *lrhk, *srow;
   int n_srow;
@@ -291,9 +295,9 @@ __global__ void predict_kernel(Dev d) {
 // block:
 //  A  dR_j/dx for both reactant slots of every reaction is formed once in
 //     shared memory (FP64) and M is gathered at the Jacobian pattern;
-//  B  A11 is factorised in shared memory by one warp; the rows of
-//     L21 = A21 U11^-1 and the columns of U12 = L11^-1 A12 are solved one
-//     warp each (entries held by lanes, resolved in order with shuffles);
+//  B  the head's factors (L11, U11, pivots, L21, U12) are computed in
+//     shared memory in the packed layout by the head program: pivots in
+//     dependency levels, every entry of a level at once (left-looking);
 //  S  the head's Schur complement A22 -= L21 U12 (sparse: about 1 % of a
 //     dense product) is applied panel by panel from shared memory: U12's
 //     panel columns as a dense tile, L21 in compact row order, one warp per
@@ -303,12 +307,32 @@ __global__ void predict_kernel(Dev d) {
 //     update is a register-tiled GEMM.
 // Inverse pivots replace the diagonal.
 // ---------------------------------------------------------------------------
+// Optional per-phase cycle counters of the refresh kernel (build option
+// SM_PHASE_CLOCKS, see build.py): thread 0 of every CTA adds the clock64()
+// cycles between consecutive phase marks (taken right after the CTA-wide
+// barriers that end the phases) to g_phase_cycles[phase]; slot 15 counts the
+// refreshed cells.  Compiled out otherwise.
+constexpr int kPhaseSlots = 16;
+#ifdef SM_PHASE_CLOCKS
+__device__ unsigned long long g_phase_cycles[kPhaseSlots];
+#define PHASE_START() long long ph_t = clock64()
+#define PHASE_MARK(k)                                                                         \
+  do {                                                                                        \
+    if (threadIdx.x == 0) {                                                                   \
+      const long long ph_now = clock64();                                                     \
+      atomicAdd(&g_phase_cycles[(k)], (unsigned long long)(ph_now - ph_t));                   \
+      ph_t = ph_now;                                                                          \
+    }                                                                                         \
+  } while (0)
+#else
+#define PHASE_START() do {} while (0)
+#define PHASE_MARK(k) do {} while (0)
+#endif
+
 constexpr int kRefreshThreads = 256;
 constexpr int kNB = 32;
 constexpr int kTM = 4, kTN = 4;
 constexpr int kBM = 16 * kTM, kBN = 16 * kTN;
-constexpr int kHeadG = 4;                 // head entries held per lane
-constexpr int kHeadLanes = 32 * kHeadG;   // longest L21 row / U12 column held in a warp
 constexpr int kPS = 3;                    // panels per pass of the head Schur complement (phase S)
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -317,11 +341,11 @@ __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b *
 struct RefreshPlan {
   int pitch;          // column pitch of the panel buffer
   int upitch;         // row pitch of the U block buffer
-  int n_u12;          // staged U12 entries (head rows, tail columns)
-  int n_l21;          // L21 entries (tail rows, head columns)
-  int l21_off;        // byte offset of the compact L21 (values, then u16 head columns) in phase B/S
   int n_panels;       // 32-wide panels of the trailing block
-  bool head_smem;     // phase B with A11 in shared memory (else pivot by pivot)
+  int hv_off;         // byte offset of the packed head factors H in phases B / S
+  int ix_off;         // byte offset of the Schur pass's staged indices (after H)
+  int n_l21, n_u12;   // L21 / U12 entries
+  bool head_smem;     // phase B runs the head program in shared memory (else pivot by pivot)
   size_t bytes;
 };
 
@@ -438,25 +462,25 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
   T* Pt = reinterpret_cast<T*>(smem_raw);           // panel, column-major, kNB columns
   T* U = Pt + (size_t)kNB * pitch;                  // U12 block, kNB rows, pitch upitch
   const int upitch = plan.upitch;
-  T* su_val = U + (size_t)kNB * upitch;             // U12 entries of the head rows (phase B on)
-  int* su_off = reinterpret_cast<int*>(su_val + plan.n_u12);
-  unsigned short* su_col = reinterpret_cast<unsigned short*>(su_off + h * np1);
-  double* dR = reinterpret_cast<double*>(smem_raw); // phase A: [n_r][2] (before the U12 stage)
+  double* dR = reinterpret_cast<double*>(smem_raw); // phase A: [n_r][2]
   float* wsf;
   float* wif;
-  T* A11 = reinterpret_cast<T*>(smem_raw);          // phase B: h x h (below su_val)
+  T* Hv = reinterpret_cast<T*>(smem_raw + plan.hv_off);  // phases B / S: packed head factors
+  // phase S indices, staged after H: per L21 entry its head column, per U12
+  // entry its tail column, per head row and panel the start of its U12 entries
+  unsigned short* sx_l21 = reinterpret_cast<unsigned short*>(smem_raw + plan.ix_off);
+  unsigned short* sx_u12 = sx_l21 + plan.n_l21;
+  int* sx_off = reinterpret_cast<int*>(smem_raw + plan.ix_off + 4 * ((plan.n_l21 + plan.n_u12 + 1) / 2));
   double* coef = dR + 2 * n_r;                      // (double)(int8_t)i, J coefficients
   wsf = reinterpret_cast<float*>(coef + 256);
   wif = wsf + n;
-  // compact L21 (tail rows' head entries, row order): phase B writes, phase S reads
-  T* l21s = reinterpret_cast<T*>(smem_raw + plan.l21_off);
-  unsigned short* l21k = reinterpret_cast<unsigned short*>(l21s + plan.n_l21);
   const int count = d.counters[0];
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t c = d.list[e];
     T* A = static_cast<T*>(d.lu) + (d.lu_cta ? (int64_t)blockIdx.x : c) * d.lu_stride;
     T* P = d.lup ? static_cast<T*>(d.lup) + (int64_t)d.slot_cell[c] * d.lup_stride : nullptr;
     T* D = P ? P + d.p_d : nullptr;   // packed tail block, column-major
+    PHASE_START();
     const double gamma = d.gam[c];
     // zero the dense trailing block and the head's pattern entries
     for (int r = warp; r < nt; r += nwarps) {
@@ -486,6 +510,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         wif[s] = (float)(1.0 / wv);
       }
     __syncthreads();
+    PHASE_MARK(0);   // zero the working matrix, dR/dx, weights
     // M_ij = delta_ij - gamma sum_terms coef dR, stored in elimination order
     // (W M W^-1 with this step's error weights, scaled in FP32, when mixed)
     auto store_m = [&](const int4 ds, double acc) {
@@ -524,142 +549,45 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       if (lb) store_m(db, ab);
     }
     __syncthreads();
-    // ---- phase B: sparse head
+    PHASE_MARK(1);   // Jacobian gather, M = I - gamma J
+    // ---- phase B: sparse head.  The head program (see LUSymbolic) computes
+    // every head factor entry in the packed layout, in shared memory: level
+    // by level, first the level's pivots (stored inverted), then the U rows
+    // and L columns of those pivots, each entry a thread's
+    //   a - sum of its product terms (times the inverse pivot for L).
     if (plan.head_smem) {
-      for (int i = tid; i < h * h; i += nthr) A11[i] = T(0);
-      __syncthreads();
-      for (int kp = warp; kp < h; kp += nwarps) {
-        for (int p = __ldg(d.lptr + kp) + lane; p < __ldg(d.lptr + kp + 1); p += 32) {
-          const int i = __ldg(d.lidx + p);
-          if (i < h) A11[i * h + kp] = A[(int64_t)i * ldm + kp];
-        }
-        for (int p = __ldg(d.uptr + kp) + lane; p < __ldg(d.uptr + kp + 1); p += 32) {
-          const int j = __ldg(d.uidx + p);
-          if (j < h) A11[kp * h + j] = A[(int64_t)kp * ldm + j];
-        }
-        if (lane == 0) A11[kp * h + kp] = A[(int64_t)kp * ldm + kp];
-      }
-      __syncthreads();
-      if (warp == 0) {
-        for (int kp = 0; kp < h; ++kp) {
-          const T inv = T(1) / A11[kp * h + kp];
-          const int l0 = __ldg(d.lptr + kp), l1 = __ldg(d.lptr + kp + 1);
-          const int u0 = __ldg(d.uptr + kp), u1 = __ldg(d.uptr + kp + 1);
-          for (int p = l0 + lane; p < l1; p += 32) {
-            const int i = __ldg(d.lidx + p);
-            if (i < h) {
-              const T l = A11[i * h + kp] * inv;
-              A11[i * h + kp] = l;
-              for (int q = u0; q < u1; ++q) {
-                const int j = __ldg(d.uidx + q);
-                if (j >= h) break;
-                A11[i * h + j] -= l * A11[kp * h + j];
-              }
-            }
-          }
-          __syncwarp();
-          if (lane == 0) A11[kp * h + kp] = inv;
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-      for (int r = warp; r < h; r += nwarps)
-        for (int q = lane; q < h; q += 32) A[(int64_t)r * ldm + q] = A11[r * h + q];
-      // L21 rows (warp per row): l_ik = (a_ik - sum_{m<k} l_im u_mk) / u_kk
-      for (int i = h + warp; i < n; i += nwarps) {
-        T* Ai = A + (int64_t)i * ldm;
-        const int p0 = __ldg(d.lrptr + i), cnt = __ldg(d.lrhead + i - h);
-        int kc[kHeadG];
-        T av[kHeadG], acc[kHeadG];
-#pragma unroll
-        for (int g = 0; g < kHeadG; ++g) {
-          const int q = lane + 32 * g;
-          kc[g] = q < cnt ? __ldg(d.lridx + p0 + q) : 0;
-          av[g] = q < cnt ? Ai[kc[g]] : T(0);
-          acc[g] = T(0);
-        }
-        for (int q = 0; q < cnt; ++q) {
-          const int gq = q >> 5, src = q & 31;
-          T mine = T(0), piv = T(0);
-          int kq = 0;
-#pragma unroll
-          for (int g = 0; g < kHeadG; ++g)
-            if (g == gq) {
-              mine = av[g] - acc[g];
-              kq = kc[g];
-            }
-          kq = shfl(kq, src);
-          piv = A11[kq * h + kq];
-          const T lq = shfl(mine, src) * piv;
-#pragma unroll
-          for (int g = 0; g < kHeadG; ++g) {
-            if (g == gq && lane == src) av[g] = lq;
-            const int qq = lane + 32 * g;
-            if (qq > q && qq < cnt) acc[g] += lq * A11[kq * h + kc[g]];
-          }
-        }
-        const int o = __ldg(d.lrhoff + i - h);
-#pragma unroll
-        for (int g = 0; g < kHeadG; ++g)
-          if (lane + 32 * g < cnt) {
-            Ai[kc[g]] = av[g];
-            l21s[o + lane + 32 * g] = av[g];
-            l21k[o + lane + 32 * g] = (unsigned short)kc[g];
-          }
-      }
-      // U12 columns (warp per column): u_kj = a_kj - sum_{m<k} l_km u_mj
-      for (int j = h + warp; j < n; j += nwarps) {
-        const int q0 = __ldg(d.ucptr + j - h), cnt = __ldg(d.ucptr + j - h + 1) - q0;
-        int kr[kHeadG];
-        T av[kHeadG], acc[kHeadG];
-#pragma unroll
-        for (int g = 0; g < kHeadG; ++g) {
-          const int q = lane + 32 * g;
-          kr[g] = q < cnt ? __ldg(d.ucidx + q0 + q) : 0;
-          av[g] = q < cnt ? A[(int64_t)kr[g] * ldm + j] : T(0);
-          acc[g] = T(0);
-        }
-        for (int q = 0; q < cnt; ++q) {
-          const int gq = q >> 5, src = q & 31;
-          T mine = T(0);
-          int kq = 0;
-#pragma unroll
-          for (int g = 0; g < kHeadG; ++g)
-            if (g == gq) {
-              mine = av[g] - acc[g];
-              kq = kr[g];
-            }
-          const T uq = shfl(mine, src);
-          kq = shfl(kq, src);
-#pragma unroll
-          for (int g = 0; g < kHeadG; ++g) {
-            if (g == gq && lane == src) av[g] = uq;
-            const int qq = lane + 32 * g;
-            if (qq > q && qq < cnt) acc[g] += A11[kr[g] * h + kq] * uq;
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < kHeadG; ++g)
-          if (lane + 32 * g < cnt) A[(int64_t)kr[g] * ldm + j] = av[g];
-      }
-      __syncthreads();
-      // stage U12 (values, columns, per-panel offsets) for phase C
+      for (int e = tid; e < plan.n_l21; e += nthr) sx_l21[e] = (unsigned short)__ldg(d.lrhk + e);
       for (int kr = warp; kr < h; kr += nwarps) {
-        const int q0 = __ldg(d.uoff + kr * np1), o = __ldg(d.u12off + kr);
-        const int cnt = __ldg(d.uptr + kr + 1) - q0;
-        const T* Ak = A + (int64_t)kr * ldm;
-        for (int q = lane; q < cnt; q += 32) {
-          const int j = __ldg(d.uidx + q0 + q);
-          su_val[o + q] = Ak[j];
-          su_col[o + q] = (unsigned short)(j - h);
-        }
-        for (int b = lane; b < np1; b += 32) su_off[kr * np1 + b] = o + __ldg(d.uoff + kr * np1 + b) - q0;
+        const int base = __ldg(d.uoff + kr * np1), o12 = __ldg(d.u12off + kr), cnt = __ldg(d.u12off + kr + 1) - o12;
+        for (int q = lane; q < cnt; q += 32) sx_u12[o12 + q] = (unsigned short)(__ldg(d.uidx + base + q) - h);
+        for (int b = lane; b < np1; b += 32) sx_off[kr * np1 + b] = o12 + __ldg(d.uoff + kr * np1 + b) - base;
       }
-      __syncthreads();
+      for (int l = 0; l < d.n_hlev; ++l) {
+        for (int part = 0; part < 2; ++part) {
+          const int o1 = __ldg(d.hop_ptr + 2 * l + part + 1);
+          for (int o = __ldg(d.hop_ptr + 2 * l + part) + tid; o < o1; o += nthr) {
+            const int4 op = __ldg(d.hop + o);
+            T v = A[op.y];
+            for (int t = op.z; t < op.w; ++t) {
+              const int2 tm = __ldg(d.hterm + t);
+              v -= Hv[tm.x] * Hv[tm.y];
+            }
+            if (part == 0) {
+              v = T(1) / v;
+            } else {
+              const int pv = __ldg(d.hop_piv + o);
+              if (pv >= 0) v *= Hv[pv];
+            }
+            Hv[op.x] = v;
+          }
+          __syncthreads();
+        }
+      }
+      PHASE_MARK(2);   // head program
       // ---- phase S: A22 -= L21 U12, one 32-column panel at a time.  U12's
-      // panel columns are expanded into a dense h x 32 tile (over A11, no
-      // longer needed); each tail row with head entries is one warp's: lanes
-      // are the panel's columns, the row's (l, k) pairs come from shared memory.
+      // panel columns are expanded into a dense h x 32 tile (in front of H);
+      // each tail row with head entries is one warp's: lanes are the panel's
+      // columns, the row's L21 values come from H.
       T* Ut = reinterpret_cast<T*>(smem_raw);
       for (int q0 = 0; q0 < plan.n_panels; q0 += kPS) {
         // kPS panels per pass: tile [j][k][32] for panel q0 + j
@@ -667,10 +595,11 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         for (int e = tid; e < np * h * kNB; e += nthr) Ut[e] = T(0);
         __syncthreads();
         for (int kr = warp; kr < h; kr += nwarps) {
-          const int e1 = su_off[kr * np1 + q0 + np];
-          for (int e = su_off[kr * np1 + q0] + lane; e < e1; e += 32) {
-            const int ct = (int)su_col[e] - kNB * q0;
-            Ut[((ct / kNB) * h + kr) * kNB + (ct % kNB)] = su_val[e];
+          // row kr's packed U12 entries of panels q0 .. q0 + np - 1
+          const int e1 = sx_off[kr * np1 + q0 + np];
+          for (int e = sx_off[kr * np1 + q0] + lane; e < e1; e += 32) {
+            const int ct = (int)sx_u12[e] - kNB * q0;
+            Ut[((ct / kNB) * h + kr) * kNB + (ct % kNB)] = Hv[d.p_u12 + e];
           }
         }
         __syncthreads();
@@ -703,8 +632,8 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
 #pragma unroll
             for (int j = 0; j < kPS; ++j) acc[j] = T(0);
             for (int e = 0; e < cnt; ++e) {
-              const T l = l21s[o + e];
-              const T* ut = Ut + (int)l21k[o + e] * kNB + lane;
+              const T l = Hv[d.p_l21 + o + e];
+              const T* ut = Ut + (int)sx_l21[o + e] * kNB + lane;
 #pragma unroll
               for (int j = 0; j < kPS; ++j)
                 if (j < np) acc[j] += l * ut[j * h * kNB];
@@ -738,9 +667,22 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         __syncthreads();
       }
     }
-    // the head's factors are final: copy them into the packed layout of the
-    // substitution (L11, U11, inverse pivots, L21, U12)
-    if (P) {
+    PHASE_MARK(3);   // head Schur complement (or the pivot-by-pivot head)
+    // the head's factors are final.  Packed output: copy them out (from H, or
+    // from the dense matrix after the pivot-by-pivot head); dense output: put
+    // H's values back at their dense positions
+    if (plan.head_smem) {
+      if (P) {
+        for (int i = tid; i < d.p_d; i += nthr) P[i] = Hv[i];
+      } else {
+        const int o1 = __ldg(d.hop_ptr + 2 * d.n_hlev);
+        for (int o = tid; o < o1; o += nthr) {
+          const int4 op = __ldg(d.hop + o);
+          A[op.y] = Hv[op.x];
+        }
+      }
+      __syncthreads();
+    } else if (P) {
       __syncthreads();
       for (int i = warp; i < h; i += nwarps) {
         const T* Ai = A + (int64_t)i * ldm;
@@ -758,6 +700,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         for (int q = lane; q < cnt; q += 32) P[d.p_l21 + o + q] = Ai[__ldg(d.lridx + p0 + q)];
       }
     }
+    PHASE_MARK(4);   // packed head factors
     // ---- phase C: dense trailing block, blocked right-looking LU
     for (int pb = 0; pb * kNB < nt; ++pb) {
       const int p0 = h + pb * kNB;
@@ -768,6 +711,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       for (int a = m + tid; a < pitch; a += nthr)
         for (int b = 0; b < w; ++b) Pt[b * pitch + a] = T(0);
       __syncthreads();
+      PHASE_MARK(5);   // panel loads
       if (sizeof(T) == 4 && w == kNB) {
         // full FP32 panel.  (1) warp 0 factors the kNB x kNB diagonal block in
         // registers (lane = row, pivot rows broadcast by shuffles); (2) every
@@ -825,6 +769,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
         }
         __syncthreads();
       }
+      PHASE_MARK(6);   // panel LU
       if (D) {
         // the panel's columns (diagonal block and L below it) are final
         for (int b = warp; b < w; b += nwarps)
@@ -839,6 +784,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
           for (int b = lane; b < rp; b += 32)
             U[a * upitch + b] = b < r ? A[(int64_t)(p0 + a) * ldm + p0 + w + b] : T(0);
         __syncthreads();
+        PHASE_MARK(7);   // panel stored, U block loaded
         // U12 = L11^-1 A12, one thread per column
         if (w == kNB) {
           for (int b = tid; b < r; b += nthr) {
@@ -860,6 +806,7 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
             }
         }
         __syncthreads();
+        PHASE_MARK(8);   // U block solved
         if (D) {
           // the panel's U rows are final: column b of the block, rows p0..p0+w
           for (int e = tid; e < r * 32; e += nthr) {
@@ -879,38 +826,51 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
             done = true;
           }
         }
+        // 64 x 64 tiles of the trailing block in turn, a 4 x 4 sub-tile per
+        // thread; the next tile's values of A are loaded while this tile's
+        // products are formed
         const int ty = tid / 16, tx = tid % 16;
-        for (int t0 = 0; t0 < (done ? 0 : r); t0 += kBM)
-          for (int u0 = 0; u0 < r; u0 += kBN) {
-            const int i0 = t0 + ty * kTM, j0 = u0 + tx * kTN;
-            if (i0 >= r || j0 >= r) continue;
-            T acc[kTM][kTN];
+        const int nbu = (r + kBN - 1) / kBN, ntile = done ? 0 : ((r + kBM - 1) / kBM) * nbu;
+        T nxt[kTM][kTN];
+        auto load_c = [&](int tt) {
+          const int i0 = (tt / nbu) * kBM + ty * kTM, j0 = (tt % nbu) * kBN + tx * kTN;
+#pragma unroll
+          for (int a = 0; a < kTM; ++a)
+#pragma unroll
+            for (int b = 0; b < kTN; ++b)
+              nxt[a][b] = (i0 + a < r && j0 + b < r) ? A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] : T(0);
+        };
+        if (ntile > 0) load_c(0);
+        for (int tt = 0; tt < ntile; ++tt) {
+          T acc[kTM][kTN];
+#pragma unroll
+          for (int a = 0; a < kTM; ++a)
+#pragma unroll
+            for (int b = 0; b < kTN; ++b) acc[a][b] = nxt[a][b];
+          if (tt + 1 < ntile) load_c(tt + 1);
+          const int i0 = (tt / nbu) * kBM + ty * kTM, j0 = (tt % nbu) * kBN + tx * kTN;
+          if (i0 >= r || j0 >= r) continue;
+          const T* lp = Pt + w + i0;
+          const T* up = U + j0;
+          for (int kk = 0; kk < w; ++kk) {
+            Vec4<T> lv, uv;
+            lv.load(lp + kk * pitch);
+            uv.load(up + kk * upitch);
 #pragma unroll
             for (int a = 0; a < kTM; ++a)
 #pragma unroll
-              for (int b = 0; b < kTN; ++b)
-                acc[a][b] = (i0 + a < r && j0 + b < r)
-                                ? A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] : T(0);
-            const T* lp = Pt + w + i0;
-            const T* up = U + j0;
-            for (int kk = 0; kk < w; ++kk) {
-              Vec4<T> lv, uv;
-              lv.load(lp + kk * pitch);
-              uv.load(up + kk * upitch);
-#pragma unroll
-              for (int a = 0; a < kTM; ++a)
-#pragma unroll
-                for (int b = 0; b < kTN; ++b) acc[a][b] -= lv.a[a] * uv.a[b];
-            }
-#pragma unroll
-            for (int a = 0; a < kTM; ++a)
-#pragma unroll
-              for (int b = 0; b < kTN; ++b)
-                if (i0 + a < r && j0 + b < r)
-                  A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] = acc[a][b];
+              for (int b = 0; b < kTN; ++b) acc[a][b] -= lv.a[a] * uv.a[b];
           }
+#pragma unroll
+          for (int a = 0; a < kTM; ++a)
+#pragma unroll
+            for (int b = 0; b < kTN; ++b)
+              if (i0 + a < r && j0 + b < r)
+                A[(int64_t)(p0 + w + i0 + a) * ldm + p0 + w + j0 + b] = acc[a][b];
+        }
       }
       __syncthreads();
+      PHASE_MARK(9);   // trailing update
     }
     if (tid == 0) {
       d.gam_J[c] = gamma;
@@ -920,6 +880,10 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       d.jac_evals[c] += 1;
     }
     __syncthreads();
+#ifdef SM_PHASE_CLOCKS
+    if (tid == 0) atomicAdd(&g_phase_cycles[kPhaseSlots - 1], 1ull);
+#endif
+    PHASE_MARK(10);  // epilogue
   }
 }
 
@@ -2492,6 +2456,8 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.n_flev = (int)lu.flev_ptr.size() - 1; d.n_blev = (int)lu.blev_ptr.size() - 1;
   d.u11ptr = lu.d_u11ptr.as<int>(); d.flev_ptr = lu.d_flev_ptr.as<int>(); d.flev = lu.d_flev.as<int>();
   d.blev_ptr = lu.d_blev_ptr.as<int>(); d.blev = lu.d_blev.as<int>();
+  d.hop_ptr = lu.d_hop_ptr.as<int>(); d.hop_piv = lu.d_hop_piv.as<int>(); d.hop = lu.d_hop.as<int4>();
+  d.hterm = lu.d_hterm.as<int2>(); d.n_hlev = lu.n_hlev;
   d.perm = lu.d_perm.as<int>(); d.iperm = lu.d_iperm.as<int>();
   d.lptr = lu.d_lptr.as<int>(); d.lidx = lu.d_lidx.as<int>();
   d.uptr = lu.d_uptr.as<int>(); d.uidx = lu.d_uidx.as<int>();
@@ -2547,32 +2513,20 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
     pl.n_panels = (nt + kNB - 1) / kNB;
     pl.upitch = round_up(std::max(nt - kNB, 4), 4);
     while (pl.upitch % 32 != 8) pl.upitch += 4;
-    pl.n_l21 = lu.lrhoff.empty() ? 0 : lu.lrhoff.back();
-    pl.n_u12 = 0;
-    for (int k2 = 0; k2 < lu.head; ++k2) pl.n_u12 += lu.uptr[k2 + 1] - lu.uoff[(size_t)k2 * (pl.n_panels + 1)];
-    const size_t stage_u12 = (esz + 2) * (size_t)pl.n_u12 + sizeof(int) * (size_t)lu.head * (pl.n_panels + 1) + 16;
-    const size_t tail = esz * (size_t)kNB * (pl.pitch + pl.upitch) + stage_u12;
+    const size_t tail = esz * (size_t)kNB * (pl.pitch + pl.upitch);
     const size_t stage = sizeof(double) * (2 * (size_t)net->n_r + 256) + sizeof(float) * 2 * (size_t)n;
-    const size_t a11 = esz * (size_t)lu.head * lu.head;
-    int max_l21 = 0, max_u12 = 0;
-    for (int i = lu.head; i < n; ++i) {
-      int cnt = 0;
-      for (int p = lu.lrptr[i]; p < lu.lrptr[i + 1] && lu.lridx[p] < lu.head; ++p) ++cnt;
-      max_l21 = std::max(max_l21, cnt);
-    }
-    for (int j = 0; j + 1 < (int)lu.ucptr.size(); ++j) max_u12 = std::max(max_u12, lu.ucptr[j + 1] - lu.ucptr[j]);
-    // phases B and S: A11 (then the U12 panel tile), the compact L21 and the
-    // staged U12 must not overlap (U12 is staged while A11 is still read)
-    const size_t su_start = esz * (size_t)kNB * (pl.pitch + pl.upitch);
-    const size_t l21_off =
-        ((std::max(a11, esz * (size_t)lu.head * kNB * std::min(kPS, pl.n_panels)) + 15) / 16) * 16;
-    const size_t l21_end = l21_off + (esz + 2) * (size_t)pl.n_l21;
-    pl.l21_off = (int)l21_off;
-    const size_t head_b = su_start + stage_u12;
-    pl.head_smem = lu.head > 0 && l21_end <= su_start && head_b <= (size_t)smem_max &&
-                   max_l21 <= kHeadLanes && max_u12 <= kHeadLanes;
+    // phases B and S: the packed head factors H after the Schur pass's U12
+    // panel tiles (kPS panels of h x kNB)
+    const size_t ut = esz * (size_t)lu.head * kNB * std::min(kPS, pl.n_panels);
+    pl.hv_off = (int)((ut + 15) / 16 * 16);
+    pl.n_l21 = lu.lrhoff.empty() ? 0 : lu.lrhoff.back();
+    pl.n_u12 = lu.u12off.empty() ? 0 : lu.u12off.back();
+    pl.ix_off = (int)((pl.hv_off + esz * (size_t)lu.p_d + 15) / 16 * 16);
+    const size_t head_b = (size_t)pl.ix_off + 4 * (size_t)((pl.n_l21 + pl.n_u12 + 1) / 2) +
+                          sizeof(int) * (size_t)lu.head * (pl.n_panels + 1);
+    pl.head_smem = lu.head > 0 && head_b <= (size_t)smem_max && n - lu.head < 65536;
     pl.bytes = std::max(tail, stage);
-    if (pl.head_smem) pl.bytes = std::max(pl.bytes, a11);
+    if (pl.head_smem) pl.bytes = std::max(pl.bytes, head_b);
   }
   const size_t rsm = st->plan.bytes;
 
@@ -2924,4 +2878,25 @@ extern "C" sm_status sm_state_timing_reset(sm_state* st) {
   st->timed = 0;
   st->timed_ms = 0.0;
   return SM_OK;
+}
+
+extern "C" sm_status sm_phase_cycles(int32_t device, double* h_out, int32_t reset) {
+#ifdef SM_PHASE_CLOCKS
+  if (!h_out || device < 0) return SM_EINVAL;
+  Scope scope(device);
+  if (!scope.ok) return SM_ECUDA;
+  unsigned long long v[kPhaseSlots];
+  SM_TRY_CUDA(cudaMemcpyFromSymbol(v, g_phase_cycles, sizeof(v)));
+  for (int i = 0; i < kPhaseSlots; ++i) h_out[i] = (double)v[i];
+  if (reset) {
+    const unsigned long long z[kPhaseSlots] = {0};
+    SM_TRY_CUDA(cudaMemcpyToSymbol(g_phase_cycles, z, sizeof(z)));
+  }
+  return SM_OK;
+#else
+  (void)device;
+  (void)h_out;
+  (void)reset;
+  return SM_ENOTSUP;
+#endif
 }

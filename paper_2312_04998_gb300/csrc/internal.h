@@ -94,8 +94,20 @@ struct LUSymbolic {
   std::vector<int32_t> u11ptr;            // per head row: start of its U11 entries (head + 1)
   std::vector<int32_t> flev_ptr, flev;    // head rows grouped by forward-substitution level
   std::vector<int32_t> blev_ptr, blev;    // head rows grouped by backward-substitution level
+  // Head program of the refresh: the sparse head's factors (L11, U11, inverse
+  // pivots, L21, U12) computed in the packed layout, level by level.  Pivot k
+  // depends on the pivots m < k with l_km or u_mk nonzero; all pivots of one
+  // level are independent.  Per level l, ops [hop_ptr[2l], hop_ptr[2l+1]) are
+  // the level's pivots, [hop_ptr[2l+1], hop_ptr[2l+2]) its U-row and L-column
+  // entries.  An op is {packed index written, offset in the dense working
+  // matrix read, first term, end of terms}; its value is
+  //   a - sum over its terms (x, y) of H[x] * H[y]
+  // (H = the packed head values), inverted for a pivot, times H[hop_piv]
+  // (the inverse pivot) for an L entry (hop_piv = -1 otherwise).
+  std::vector<int32_t> hop_ptr, hop, hop_piv, hterm;   // hop: 4 ints per op, hterm: 2 per term
+  int32_t n_hlev = 0;
   int64_t nnz = 0, flops = 0;
-  DevArray d_u11ptr, d_flev_ptr, d_flev, d_blev_ptr, d_blev;
+  DevArray d_u11ptr, d_flev_ptr, d_flev, d_blev_ptr, d_blev, d_hop_ptr, d_hop, d_hop_piv, d_hterm;
   DevArray d_lptr, d_lidx, d_uptr, d_uidx, d_lrptr, d_lridx, d_ucptr, d_ucidx, d_jpos, d_perm, d_iperm,
       d_jrc, d_uoff, d_lrhead, d_lrhoff, d_u12off, d_lrhk, d_srow;
 };

@@ -59,6 +59,7 @@ reaction_rate_kernel(int n_r, int64_t C, const int2* __restrict__ reac, const do
   if (mask && !__syncthreads_or(act)) return;
   if (!act) return;
   const int j1 = min(n_r, (int)(blockIdx.y + 1) * kRChunk);
+#pragma unroll 4
   for (int j = blockIdx.y * kRChunk; j < j1; ++j) {
     const int2 a = __ldg(reac + j);
     double v = k[(int64_t)j * ldk + c] * y[(int64_t)a.x * ldy + c];
@@ -67,20 +68,27 @@ reaction_rate_kernel(int n_r, int64_t C, const int2* __restrict__ reac, const do
   }
 }
 
+// sum over entries [b, e) of coef * r[col]: four independent partial sums so
+// that four rate loads are in flight per thread (the FP64 gather is bound by
+// their latency, not by the FP64 pipe)
 __device__ __forceinline__ double dot_range(const uint32_t* __restrict__ ent, int b, int e,
                                             const double* __restrict__ r, int64_t ldr, int64_t c) {
-  double s0 = 0.0, s1 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int p = b;
-  for (; p + 1 < e; p += 2) {
-    const uint32_t w0 = __ldg(ent + p), w1 = __ldg(ent + p + 1);
-    s0 = fma(c_coef[w0 >> 24], r[(int64_t)(w0 & 0xFFFFFFu) * ldr + c], s0);
-    s1 = fma(c_coef[w1 >> 24], r[(int64_t)(w1 & 0xFFFFFFu) * ldr + c], s1);
+  for (; p + 3 < e; p += 4) {
+    const uint32_t w0 = __ldg(ent + p), w1 = __ldg(ent + p + 1), w2 = __ldg(ent + p + 2), w3 = __ldg(ent + p + 3);
+    const double r0 = r[(int64_t)(w0 & 0xFFFFFFu) * ldr + c], r1 = r[(int64_t)(w1 & 0xFFFFFFu) * ldr + c];
+    const double r2 = r[(int64_t)(w2 & 0xFFFFFFu) * ldr + c], r3 = r[(int64_t)(w3 & 0xFFFFFFu) * ldr + c];
+    s0 = fma(c_coef[w0 >> 24], r0, s0);
+    s1 = fma(c_coef[w1 >> 24], r1, s1);
+    s2 = fma(c_coef[w2 >> 24], r2, s2);
+    s3 = fma(c_coef[w3 >> 24], r3, s3);
   }
-  if (p < e) {
+  for (; p < e; ++p) {
     const uint32_t w0 = __ldg(ent + p);
     s0 = fma(c_coef[w0 >> 24], r[(int64_t)(w0 & 0xFFFFFFu) * ldr + c], s0);
   }
-  return s0 + s1;
+  return (s0 + s1) + (s2 + s3);
 }
 
 __global__ void __launch_bounds__(kCells * kChunks)

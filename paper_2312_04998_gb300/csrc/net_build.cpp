@@ -360,6 +360,85 @@ void build_lu_symbolic(sm_net& net) {
     lu.p_d = (int32_t)up32(lu.p_u12 + lu.u12off.back());
     lu.ldd = (int32_t)up32(nt);
     lu.p_size = up32((int64_t)lu.p_d + (int64_t)nt * lu.ldd);
+
+    // head program: packed index of every head factor entry, pivot levels,
+    // and the product terms of each entry's left-looking update
+    const int32_t ld = lu.ld;
+    std::vector<int32_t> lpos((size_t)n * std::max(h, 1), -1), upos((size_t)std::max(h, 1) * n, -1);
+    for (int32_t i = 0; i < h; ++i)
+      for (int32_t p = lu.lrptr[i]; p < lu.lrptr[i + 1]; ++p) lpos[(size_t)i * h + lu.lridx[p]] = lu.p_l11 + p;
+    for (int32_t i = h; i < n; ++i)
+      for (int32_t q = 0; q < lu.lrhead[i - h]; ++q)
+        lpos[(size_t)i * h + lu.lridx[lu.lrptr[i] + q]] = lu.p_l21 + lu.lrhoff[i - h] + q;
+    for (int32_t k = 0; k < h; ++k)
+      for (int32_t p = lu.uptr[k]; p < lu.uptr[k + 1]; ++p) {
+        const int32_t j = lu.uidx[p];
+        const int32_t q12 = lu.uoff[(size_t)k * np1];
+        upos[(size_t)k * n + j] = j < h ? lu.p_u11 + lu.u11ptr[k] + (p - lu.uptr[k])
+                                        : lu.p_u12 + lu.u12off[k] + (p - q12);
+      }
+    // U11 columns: head rows m < k with u_mk != 0
+    std::vector<std::vector<int32_t>> ucol11(h);
+    for (int32_t m = 0; m < h; ++m)
+      for (int32_t p = lu.uptr[m]; p < lu.uoff[(size_t)m * np1]; ++p) ucol11[lu.uidx[p]].push_back(m);
+    std::vector<int32_t> lev(h, 0);
+    for (int32_t k = 0; k < h; ++k) {
+      for (int32_t p = lu.lrptr[k]; p < lu.lrptr[k + 1]; ++p) lev[k] = std::max(lev[k], lev[lu.lridx[p]] + 1);
+      for (int32_t m : ucol11[k]) lev[k] = std::max(lev[k], lev[m] + 1);
+    }
+    int32_t nl = 0;
+    for (int32_t v : lev) nl = std::max(nl, v + 1);
+    lu.n_hlev = nl;
+    lu.hop.clear();
+    lu.hop_piv.clear();
+    lu.hterm.clear();
+    lu.hop_ptr.assign(1, 0);
+    auto add_op = [&](int32_t dst, int32_t src, int32_t piv, const std::vector<std::pair<int32_t, int32_t>>& t) {
+      lu.hop.push_back(dst);
+      lu.hop.push_back(src);
+      lu.hop.push_back((int32_t)lu.hterm.size() / 2);
+      for (auto& e : t) {
+        lu.hterm.push_back(e.first);
+        lu.hterm.push_back(e.second);
+      }
+      lu.hop.push_back((int32_t)lu.hterm.size() / 2);
+      lu.hop_piv.push_back(piv);
+    };
+    for (int32_t l = 0; l < nl; ++l) {
+      // pivots: u_kk = a_kk - sum_m l_km u_mk
+      for (int32_t k = 0; k < h; ++k) {
+        if (lev[k] != l) continue;
+        std::vector<std::pair<int32_t, int32_t>> t;
+        for (int32_t p = lu.lrptr[k]; p < lu.lrptr[k + 1]; ++p) {
+          const int32_t m = lu.lridx[p];
+          if (upos[(size_t)m * n + k] >= 0) t.push_back({lpos[(size_t)k * h + m], upos[(size_t)m * n + k]});
+        }
+        add_op(lu.p_dinv + k, k * ld + k, -1, t);
+      }
+      lu.hop_ptr.push_back((int32_t)lu.hop_piv.size());
+      for (int32_t k = 0; k < h; ++k) {
+        if (lev[k] != l) continue;
+        // U row k: u_kj = a_kj - sum_m l_km u_mj
+        for (int32_t p = lu.uptr[k]; p < lu.uptr[k + 1]; ++p) {
+          const int32_t j = lu.uidx[p];
+          std::vector<std::pair<int32_t, int32_t>> t;
+          for (int32_t q = lu.lrptr[k]; q < lu.lrptr[k + 1]; ++q) {
+            const int32_t m = lu.lridx[q];
+            if (upos[(size_t)m * n + j] >= 0) t.push_back({lpos[(size_t)k * h + m], upos[(size_t)m * n + j]});
+          }
+          add_op(upos[(size_t)k * n + j], k * ld + j, -1, t);
+        }
+        // L column k: l_ik = (a_ik - sum_m l_im u_mk) / u_kk
+        for (int32_t p = lu.lptr[k]; p < lu.lptr[k + 1]; ++p) {
+          const int32_t i = lu.lidx[p];
+          std::vector<std::pair<int32_t, int32_t>> t;
+          for (int32_t m : ucol11[k])
+            if (lpos[(size_t)i * h + m] >= 0) t.push_back({lpos[(size_t)i * h + m], upos[(size_t)m * n + k]});
+          add_op(lpos[(size_t)i * h + k], i * ld + k, lu.p_dinv + k, t);
+        }
+      }
+      lu.hop_ptr.push_back((int32_t)lu.hop_piv.size());
+    }
   }
   lu.jpos.resize(net.jp_col.size());
   lu.jrc.resize(net.jp_col.size());
@@ -718,6 +797,11 @@ sm_status net_upload(sm_net* net) {
   if (!lu.lrhk.empty() && (st = lu.d_lrhk.upload(lu.lrhk.data(), lu.lrhk.size() * 4)) != SM_OK) return st;
   if (!lu.srow.empty() && (st = lu.d_srow.upload(lu.srow.data(), lu.srow.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_u11ptr.upload(lu.u11ptr.data(), lu.u11ptr.size() * 4)) != SM_OK) return st;
+  if ((st = lu.d_hop_ptr.upload(lu.hop_ptr.data(), lu.hop_ptr.size() * 4)) != SM_OK) return st;
+  if (!lu.hop.empty() && (st = lu.d_hop.upload(lu.hop.data(), lu.hop.size() * 4)) != SM_OK) return st;
+  if (!lu.hop_piv.empty() && (st = lu.d_hop_piv.upload(lu.hop_piv.data(), lu.hop_piv.size() * 4)) != SM_OK)
+    return st;
+  if (!lu.hterm.empty() && (st = lu.d_hterm.upload(lu.hterm.data(), lu.hterm.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_flev_ptr.upload(lu.flev_ptr.data(), lu.flev_ptr.size() * 4)) != SM_OK) return st;
   if (!lu.flev.empty() && (st = lu.d_flev.upload(lu.flev.data(), lu.flev.size() * 4)) != SM_OK) return st;
   if ((st = lu.d_blev_ptr.upload(lu.blev_ptr.data(), lu.blev_ptr.size() * 4)) != SM_OK) return st;
