@@ -69,7 +69,11 @@ PEAK_FP64 = SM_COUNT * 4 * SM_GHZ / 1e3           # TFLOP/s
 # ncu capture in profiles/ (named there), keyed on the kernel class, the
 # precision and the hash of integrate.cu at capture time: a changed kernel
 # reports traffic null until it is captured again.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/refresh_kernel_mixed_2048cells.md: 11.46 GB in a launch that
+    # refreshed all 2048 cells
+    ("refresh", "mixed", "df9e6bcf2f2c2e87"): 5.596e6,
+}
 
 
 def args_():
@@ -84,7 +88,7 @@ def args_():
     p.add_argument("--attempts-est", type=int, default=1400,
                    help="expected attempts of one integration; slices are attempts-est / steps long")
     p.add_argument("--time-kernel", default="refresh",
-                   choices=["refresh", "rhs", "solve", "predict", "finish"])
+                   choices=["none", "refresh", "rhs", "solve", "predict", "finish"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--mixed-cells", type=int, default=16384,
