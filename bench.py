@@ -24,6 +24,8 @@ After the headline line's own measurements the same JSON line carries:
                   against one recorded forward integrate
   rhs_jac         rhs_eval per storage format / row order and jac_eval on
                   4096 cells, against the FP64-pipe ceiling
+  pdr_slab        the paper's PDR benchmark geometry (128 cells, 30 Myr) as
+                  one whole simulation, mixed and FP64
   cpu_baseline    the oracle on the host cores: 64 stratified cells, each
                   integrated over the whole interval
 
@@ -91,6 +93,8 @@ def args_():
                    choices=["none", "refresh", "rhs", "solve", "predict", "finish"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-pdr", action="store_true", help="skip the PDR-slab simulation")
+    p.add_argument("--no-tune", action="store_true", help="integrate with the default gather, untuned")
     p.add_argument("--mixed-cells", type=int, default=16384,
                    help="cells of the FP64 vs mixed comparison (0 = skip)")
     p.add_argument("--adjoint-cells", type=int, default=1024,
@@ -99,7 +103,7 @@ def args_():
                    help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
     p.add_argument("--budget-s", type=float, default=1200.0,
                    help="auxiliary measurements start only while the run is younger than this")
-    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe"],
+    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe", "pdr"],
                    help="run one auxiliary measurement alone and print it")
     p.add_argument("--phases", action="store_true",
                    help="refresh-kernel cycles per phase over one integration (phase-clock build)")
@@ -493,6 +497,52 @@ def rhs_jac_grid(B, C, dev, peaks):
             "rows": out}
 
 
+def pdr_slab(B, dev, precisions=("mixed", "fp64")):
+    """The paper's benchmark geometry with the synthetic network: the 128-cell
+    PDR slab (n_H 1e3, T 50 K, FUV field 1e5 on the photorates, A_V 1e-3 to
+    20 on a log grid, atomic start) integrated to 30 Myr, as one whole
+    simulation timed with CUDA events (sm_rates_eval_chi + sm_integrate) after
+    an untimed run that captures the graphs.  The paper's own number for its
+    PDR run (UMIST network, 468 x 6175, 2x Xeon E5-2650 v3, CRS, serial):
+    232 s, context only."""
+    import numpy as np
+    import torch
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["pdr_slab_470x6000_c128"]
+    d, T, nH, Av, y0 = make(w.name)
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+    net = B.Network(d, dev.index or 0)
+    Td, nHd, Avd = device_conditions(B, T, nH, Av, dev)
+    chid = torch.ones(ld, dtype=torch.float64, device=dev)
+    chid[:C] = w.chi
+    kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
+    y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
+    y0d[:, :C] = torch.tensor(y0, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": w.name, "cells": C, "t_end_myr": w.t_end / YEAR / 1e6, "chi": w.chi,
+           "paper_cpu_s": 232.0}
+    for prec in precisions:
+        st = B.State(net, C, precision=prec)
+        stats = B.stats_tensor(C, dev)
+        yd = y0d.clone()
+
+        def run():
+            net.rates_eval_chi(Td, nHd, Avd, chid, kd, C)
+            yd.copy_(y0d)
+            return st.integrate(kd, yd, w.t_end, C, stats)
+
+        run()
+        code, ms = timed(run, stream)
+        s = B.stats_to_numpy(stats)
+        out[prec] = {"seconds": ms * 1e-3, "cell_steps_per_s": float(s["steps"].sum()) / (ms * 1e-3),
+                     "steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
+                     "cells_ok": int((s["status"] == 0).sum()), "status": int(code)}
+        st.close()
+    net.close()
+    return out
+
+
 def peaks_(B, dev):
     """HBM: the measured copy bandwidth (MEASURED_PEAKS.json); FP64 / FP32:
     unit counts x clock, with this run's FMA-probe rates beside them."""
@@ -663,7 +713,7 @@ def main():
         fn = {"rhs": lambda: rhs_jac_grid(B, a.rhs_cells, dev, peaks_(B, dev)),
               "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
               "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
-              "probe": lambda: peaks_(B, dev)}[a.only]
+              "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev)}[a.only]
         if rank == 0:
             print(json.dumps(fn()))
         return
@@ -678,12 +728,20 @@ def main():
     T, nH, Av, y0 = T[sl], nH[sl], Av[sl], np.ascontiguousarray(y0[:, sl])
     net = B.Network(d, local)
     info = net.info()
-    state = B.State(net, C, precision=a.precision, timing_kind=a.time_kernel)
     ld = B.pad_ld(C)
     Td, nHd, Avd = device_conditions(B, T, nH, Av, dev)
     y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
     y0d[:, :C] = torch.tensor(y0, dtype=torch.float64, device=dev)
     kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
+    # measured choice of the traversals (untimed set-up): the standalone
+    # rhs_eval format and the integrator's gather (row order, cells per CTA)
+    tune = None
+    if not a.no_tune:
+        net.rates_eval(Td, nHd, Avd, kd, C)
+        fscr = torch.empty_like(y0d)
+        tune = net.autotune(kd, y0d, fscr, C)
+        del fscr
+    state = B.State(net, C, precision=a.precision, timing_kind=a.time_kernel)
     stats = B.stats_tensor(C, dev)
     per = state.opts.attempts_per_sync
     A = slice_attempts(a.attempts_est, a.steps, per)
@@ -793,6 +851,7 @@ def main():
     mixed = aux(fp64_vs_mixed, B, a.mixed_cells, dev) if a.mixed_cells > 0 else None
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
+    pdr = None if a.no_pdr else aux(pdr_slab, B, dev)
     cpu = None if a.no_cpu else aux(cpu_baseline, t_end)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -803,7 +862,8 @@ def main():
                    "t_end_yr": a.t_end_yr, "rtol": 1e-6, "atol": 1e-20, "precision": a.precision,
                    "step": f"one slice of one whole integration: {A} attempts per step, the last step until "
                            f"every cell reached t_end ({tail} attempts)",
-                   "l2": "inputs larger than L2 (k' alone is 3.1 GB per GPU)"},
+                   "l2": "inputs larger than L2 (k' alone is 3.1 GB per GPU)",
+                   "tuned": tune},
         "stats": {"cell_steps": cell_steps, "steps_per_cell": float(s["steps"].mean()),
                   "max_steps": int(s["steps"].max()), "attempts": attempts,
                   "newton_per_cell": float(s["newton_iters"].mean()),
@@ -812,7 +872,7 @@ def main():
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "peaks": peaks,
+        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "pdr_slab": pdr, "peaks": peaks,
         "wall_s": time.time() - t_start,
     }
     print(json.dumps(out))

@@ -145,12 +145,22 @@ sm_status sm_net_set_format(sm_net* net, int32_t fmt, int32_t order, int32_t sel
                             int32_t sell_sigma);
 sm_status sm_net_get_info(const sm_net* net, sm_net_info* info);
 
+/* Select the integrator's right-hand-side gather (run in every Newton
+ * iteration): CRS in row order `order` (SM_ORDER_*) with 8, 16 or 32 cells per
+ * CTA.  sm_net_autotune makes this choice by measurement; the default is the
+ * original order with 16 cells.  States keep the choice current when they
+ * capture their graph of attempts.  SM_EINVAL on other values. */
+sm_status sm_net_set_integ(sm_net* net, int32_t order, int32_t cells_per_cta);
+
 /* Result of sm_net_autotune. */
 typedef struct {
     int32_t fmt, order, sell_C, sell_sigma;  /* the selected traversal          */
     double us;                               /* its median sm_rhs_eval time     */
     int32_t candidates;                      /* traversals timed (0 if cached)  */
     int32_t cached;                          /* 1: taken from the process cache */
+    int32_t integ_order;                     /* the integrator's gather: row order */
+    int32_t integ_cells_per_cta;             /*   and cells per CTA (8, 16, 32)    */
+    double integ_us;                         /*   its median time (rate pass + gather) */
 } sm_tune_result;
 
 /* Measured choice of the sm_rhs_eval traversal (the paper's storage-format
@@ -159,7 +169,12 @@ typedef struct {
  * and sigma in {1, 8C, n_s}), runs sm_rhs_eval on the caller's device arrays
  * d_k = k'[n_r][ld], d_y = x[n_s][ld] (C cells) writing d_f = f[n_s][ld], times
  * one warm-up and five calls with CUDA events on `stream` (median), and leaves
- * the fastest selected (as sm_net_set_format would).  The choice is cached for
+ * the fastest selected (as sm_net_set_format would).  It then times the
+ * integrator's Newton-iteration right-hand side (rate pass + masked CRS
+ * gather) for CRS in each row order x 8, 16 or 32 cells per CTA on the same
+ * inputs and selects the fastest for the network's integrations; a state
+ * keeps the choice that was current when it captured its graph of attempts,
+ * so tune before integrating.  The choice is cached for
  * the process per (network content, device name, C rounded up to a power of
  * two); force = 1 measures again.  Synchronises with `stream`.  d_f is
  * scratch: it holds the last candidate's result on return.  If a candidate
@@ -197,6 +212,14 @@ sm_status sm_net_export(const sm_net* net, int32_t what, void* h_buf, size_t byt
  * results differ from alpha (T/300)^beta exp(-gamma/T) n_H by rounding only. */
 sm_status sm_rates_eval(const sm_net* net, int64_t C, const double* d_T, const double* d_nH,
                         const double* d_Av, double zeta, double* d_k, int64_t ld, void* stream);
+
+/* sm_rates_eval with a per-cell FUV field: d_chi[C] (device; NULL = 1 in every
+ * cell) multiplies the photorates, k = chi alpha exp(-gamma A_V), the
+ * illumination of the paper's PDR benchmark (chi = 1e5 Draine fields,
+ * Section 3).  Other classes as in sm_rates_eval. */
+sm_status sm_rates_eval_chi(const sm_net* net, int64_t C, const double* d_T, const double* d_nH,
+                            const double* d_Av, const double* d_chi, double zeta, double* d_k, int64_t ld,
+                            void* stream);
 
 /* Right-hand side f = S R(y) (Eq. 7) for C cells: d_k = k'[n_r][ld], d_y =
  * x[n_s][ld] -> d_f[n_s][ld], FP64, with the traversal chosen by

@@ -9,7 +9,8 @@ outside the ODE solver, as the paper's KM2 does (Section 3):
 
 * two-body and dissociative recombination:  k = alpha (T/300)^beta exp(-gamma/T)
 * cosmic ray:                               k = alpha zeta
-* photoreaction:                            k = alpha exp(-gamma A_V)
+* photoreaction:                            k = chi alpha exp(-gamma A_V)
+  (chi: the FUV field in units of the Draine field, Section 3; 1 by default)
 
 R_j = k'_j prod_{a in reactants(j)} x_a  (a species listed twice is squared,
 Eqs. 2-6), and dx/dt = S R (Eq. 7).
@@ -28,12 +29,14 @@ def order_of(desc) -> np.ndarray:
     return (desc.reactants >= 0).sum(axis=1)
 
 
-def rate_coefficients(desc, T, nH, Av, zeta=ZETA_CR) -> np.ndarray:
-    """k'[n_r, C] for cells with temperature T, density n_H and extinction A_V."""
+def rate_coefficients(desc, T, nH, Av, zeta=ZETA_CR, chi=None) -> np.ndarray:
+    """k'[n_r, C] for cells with temperature T, density n_H and extinction A_V;
+    chi (per cell, default 1) scales the photorates."""
     T = np.atleast_1d(np.asarray(T, dtype=float))
     nH = np.atleast_1d(np.asarray(nH, dtype=float))
     Av = np.atleast_1d(np.asarray(Av, dtype=float))
     C = T.shape[0]
+    chi = np.ones(C) if chi is None else np.broadcast_to(np.asarray(chi, dtype=float), (C,))
     k = np.empty((desc.n_r, C))
     order = order_of(desc)
     for j in range(desc.n_r):
@@ -44,7 +47,7 @@ def rate_coefficients(desc, T, nH, Av, zeta=ZETA_CR) -> np.ndarray:
         elif cls == 1:
             kj = np.full(C, a * zeta)
         elif cls == 2:
-            kj = a * np.exp(-g * Av)
+            kj = chi * a * np.exp(-g * Av)
         else:
             raise ValueError(f"unknown reaction class {cls}")
         k[j] = kj * nH ** (order[j] - 1)

@@ -53,7 +53,8 @@ class NetInfo_c(ct.Structure):
 
 class TuneResult_c(ct.Structure):
     _fields_ = [("fmt", ct.c_int32), ("order", ct.c_int32), ("sell_C", ct.c_int32), ("sell_sigma", ct.c_int32),
-                ("us", ct.c_double), ("candidates", ct.c_int32), ("cached", ct.c_int32)]
+                ("us", ct.c_double), ("candidates", ct.c_int32), ("cached", ct.c_int32),
+                ("integ_order", ct.c_int32), ("integ_cells_per_cta", ct.c_int32), ("integ_us", ct.c_double)]
 
 
 class Opts_c(ct.Structure):
@@ -86,12 +87,15 @@ _SIGS = [
                                             ct.POINTER(ct.c_void_p)]),
     ("sm_net_set_format", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]),
     ("sm_net_get_info", ct.c_int32, [ct.c_void_p, ct.POINTER(NetInfo_c)]),
+    ("sm_net_set_integ", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32]),
     ("sm_net_autotune", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                      ct.c_int64, ct.c_int32, ct.c_void_p, ct.POINTER(TuneResult_c)]),
     ("sm_net_export_size", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_size_t)]),
     ("sm_net_export", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_size_t]),
     ("sm_rates_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                    ct.c_double, ct.c_void_p, ct.c_int64, ct.c_void_p]),
+    ("sm_rates_eval_chi", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                       ct.c_void_p, ct.c_double, ct.c_void_p, ct.c_int64, ct.c_void_p]),
     ("sm_rhs_eval", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                  ct.c_int64, ct.c_void_p]),
     ("sm_rhs_eval_static", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
@@ -244,6 +248,14 @@ class Network:
                 raise ValueError("batched tensors must share the row stride ld with unit column stride")
         return ld
 
+    def rates_eval_chi(self, T, nH, Av, chi, k, C=None, zeta=1.3e-17):
+        """sm_rates_eval_chi: photorates scaled by the per-cell FUV field chi
+        (device tensor, or None for 1)."""
+        C = T.shape[0] if C is None else C
+        _check(lib().sm_rates_eval_chi(self.h, int(C), _dptr(T), _dptr(nH), _dptr(Av),
+                                       _dptr(chi) if chi is not None else None, float(zeta),
+                                       _dptr(k), int(self._ld(k)), _stream(k.device)), "sm_rates_eval_chi")
+
     def rates_eval(self, T, nH, Av, k, C=None, zeta=1.3e-17):
         C = T.shape[0] if C is None else C
         _check(lib().sm_rates_eval(self.h, int(C), _dptr(T), _dptr(nH), _dptr(Av), float(zeta),
@@ -259,7 +271,13 @@ class Network:
         inv_f = {v: k_ for k_, v in FMT.items()}
         inv_o = {v: k_ for k_, v in ORDER.items()}
         return {"fmt": inv_f[r.fmt], "order": inv_o[r.order], "sell_C": r.sell_C, "sell_sigma": r.sell_sigma,
-                "us": r.us, "candidates": r.candidates, "cached": bool(r.cached)}
+                "us": r.us, "candidates": r.candidates, "cached": bool(r.cached),
+                "integ_order": inv_o[r.integ_order], "integ_cells_per_cta": r.integ_cells_per_cta,
+                "integ_us": r.integ_us}
+
+    def set_integ(self, order="none", cells_per_cta=16):
+        """The integrator's gather: CRS row order and cells per CTA (8, 16, 32)."""
+        _check(lib().sm_net_set_integ(self.h, ORDER[order], int(cells_per_cta)), "sm_net_set_integ")
 
     def rhs_eval(self, k, y, f, C):
         ld = self._ld(k, y, f)

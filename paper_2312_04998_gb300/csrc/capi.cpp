@@ -65,11 +65,16 @@ void release_all(sm_net* net) {
   f.d_packed.release();
   f.d_aux.release();
   f.d_chunk.release();
-  Format& g = net->integ;
-  g.d_ptr.release();
-  g.d_packed.release();
-  g.d_aux.release();
-  g.d_chunk.release();
+  f.d_chunk64.release();
+  f.d_chunk16.release();
+  for (Format& g : net->integ_fmt) {
+    g.d_ptr.release();
+    g.d_packed.release();
+    g.d_aux.release();
+    g.d_chunk.release();
+    g.d_chunk64.release();
+    g.d_chunk16.release();
+  }
   LUSymbolic& lu = net->lu;
   lu.d_lrptr.release();
   lu.d_lridx.release();
@@ -176,6 +181,24 @@ sm_status sm_net_set_format(sm_net* net, int32_t fmt, int32_t order, int32_t sel
   return net_select_format(net, fmt, order, sell_C, sell_sigma);
 }
 
+sm_status sm_net_set_integ(sm_net* net, int32_t order, int32_t cells_per_cta) {
+  if (!net || order < SM_ORDER_NONE || order > SM_ORDER_RCM ||
+      (cells_per_cta != 8 && cells_per_cta != 16 && cells_per_cta != 32))
+    return SM_EINVAL;
+  sm_status st;
+  if (net->device >= 0) {
+    DeviceScope ds(net->device);
+    if (!ds.ok) return SM_ECUDA;
+    st = integ_format(net, order);
+  } else {
+    st = integ_format(net, order);
+  }
+  if (st != SM_OK) return st;
+  net->integ_order = order;
+  net->integ_kc = cells_per_cta;
+  return SM_OK;
+}
+
 sm_status sm_net_get_info(const sm_net* net, sm_net_info* info) {
   if (!net || !info) return SM_EINVAL;
   *info = net->info;
@@ -238,7 +261,17 @@ sm_status sm_rates_eval(const sm_net* net, int64_t C, const double* d_T, const d
   if (C > 0 && (!d_T || !d_nH || !d_Av || !d_k)) return SM_EINVAL;
   DeviceScope ds(net->device);
   if (!ds.ok) return SM_ECUDA;
-  return launch_rates(net, C, d_T, d_nH, d_Av, zeta, d_k, ld, (cudaStream_t)stream);
+  return launch_rates(net, C, d_T, d_nH, d_Av, nullptr, zeta, d_k, ld, (cudaStream_t)stream);
+}
+
+sm_status sm_rates_eval_chi(const sm_net* net, int64_t C, const double* d_T, const double* d_nH,
+                            const double* d_Av, const double* d_chi, double zeta, double* d_k, int64_t ld,
+                            void* stream) {
+  if (!device_ready(net) || !ld_ok(C, ld)) return SM_EINVAL;
+  if (C > 0 && (!d_T || !d_nH || !d_Av || !d_k)) return SM_EINVAL;
+  DeviceScope ds(net->device);
+  if (!ds.ok) return SM_ECUDA;
+  return launch_rates(net, C, d_T, d_nH, d_Av, d_chi, zeta, d_k, ld, (cudaStream_t)stream);
 }
 
 sm_status sm_rhs_eval(const sm_net* net, int64_t C, const double* d_k, const double* d_y,

@@ -58,9 +58,11 @@ struct Format {
   // Packed device entries: column (or row) in the low 24 bits, signed
   // coefficient in the high 8 bits.
   std::vector<uint32_t> packed;
-  // CRS warp partition: per chunk the first nonzero (n_chunks + 1 entries).
-  std::vector<int32_t> chunk_nz;
-  DevArray d_ptr, d_packed, d_aux, d_chunk;
+  // CRS partitions: per chunk the first nonzero, for 32 chunks (chunk_nz,
+  // the default 16-cell gather) and for 64 / 16 chunks (the 8- and 32-cell
+  // gathers of the integrator), n_chunks + 1 entries each.
+  std::vector<int32_t> chunk_nz, chunk_nz64, chunk_nz16;
+  DevArray d_ptr, d_packed, d_aux, d_chunk, d_chunk64, d_chunk16;
 };
 
 // Symbolic LU of the Newton matrix M = I - gamma J (no pivoting).
@@ -125,7 +127,12 @@ struct sm_net {
   // Row orders and column orders for SM_ORDER_NONE / NNZ / RCM.
   std::vector<int32_t> row_order[3], col_order[3];
   Format cur;
-  Format integ;  // CRS in the original order, used inside the integrator
+  // The integrator's masked CRS gather: CRS in each row order (NONE, NNZ,
+  // RCM; built on first use and kept for the network's life, so that a
+  // captured graph never refers to released arrays), the selected order and
+  // the cells per CTA of the gather (8, 16 or 32), chosen by sm_net_autotune.
+  Format integ_fmt[3];
+  int32_t integ_order = SM_ORDER_NONE, integ_kc = 16;
   // Jacobian pattern (CRS, species order) and contribution list per entry:
   // term = coef * k'[j] * (partner >= 0 ? y[partner] : 1).
   std::vector<int32_t> jp_ptr, jp_col, jt_ptr, jt_rx, jt_partner;
@@ -152,10 +159,12 @@ sm_status net_upload(sm_net* net);
 sm_status net_select_format(sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma);
 sm_status build_format(const sm_net* net, int32_t fmt, int32_t order, int32_t C, int32_t sigma,
                        Format* out);
+// Builds (once) the integrator's CRS format in row order `order`.
+sm_status integ_format(sm_net* net, int32_t order);
 
 // Kernel launchers (one per .cu file).
 sm_status launch_rates(const sm_net* net, int64_t C, const double* T, const double* nH,
-                       const double* Av, double zeta, double* k, int64_t ld, cudaStream_t s);
+                       const double* Av, const double* chi, double zeta, double* k, int64_t ld, cudaStream_t s);
 sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double* y,
                      double* f, int64_t ld, double* scratch, int64_t ld_scratch, cudaStream_t s);
 // Masked CRS right-hand side for the integrator: cells whose mask word has

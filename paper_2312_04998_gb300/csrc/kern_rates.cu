@@ -13,13 +13,14 @@ constexpr int kRatesChunk = 64;
 
 __global__ void __launch_bounds__(kRatesThreads)
 rates_kernel(int n_r, int64_t C, const RatePar* __restrict__ par, const double* __restrict__ T,
-             const double* __restrict__ nH, const double* __restrict__ Av, double zeta,
-             double* __restrict__ k, int64_t ld) {
+             const double* __restrict__ nH, const double* __restrict__ Av, const double* __restrict__ chi,
+             double zeta, double* __restrict__ k, int64_t ld) {
   const int64_t c = (int64_t)blockIdx.x * kRatesThreads + threadIdx.x;
   if (c >= C) return;
   const int j0 = blockIdx.y * kRatesChunk;
   const int j1 = min(n_r, j0 + kRatesChunk);
   const double t = T[c], n = nH[c], av = Av[c];
+  const double fuv = chi ? chi[c] : 1.0;   // FUV field on the photorates
   const double lt = log(t * (1.0 / 300.0));
   const double it = 1.0 / t;
   for (int j = j0; j < j1; ++j) {
@@ -31,7 +32,7 @@ rates_kernel(int n_r, int64_t C, const RatePar* __restrict__ par, const double* 
     } else if (cls == SM_COSMIC_RAY) {
       v = p.x * zeta;
     } else {
-      v = p.x * exp(-p.z * av);
+      v = fuv * p.x * exp(-p.z * av);
     }
     k[(int64_t)j * ld + c] = v;
   }
@@ -40,11 +41,11 @@ rates_kernel(int n_r, int64_t C, const RatePar* __restrict__ par, const double* 
 }  // namespace
 
 sm_status launch_rates(const sm_net* net, int64_t C, const double* T, const double* nH,
-                       const double* Av, double zeta, double* k, int64_t ld, cudaStream_t s) {
+                       const double* Av, const double* chi, double zeta, double* k, int64_t ld, cudaStream_t s) {
   if (C == 0) return SM_OK;
   dim3 grid((unsigned)((C + kRatesThreads - 1) / kRatesThreads),
             (unsigned)((net->n_r + kRatesChunk - 1) / kRatesChunk));
-  rates_kernel<<<grid, kRatesThreads, 0, s>>>(net->n_r, C, net->d_rate.as<RatePar>(), T, nH, Av,
+  rates_kernel<<<grid, kRatesThreads, 0, s>>>(net->n_r, C, net->d_rate.as<RatePar>(), T, nH, Av, chi,
                                                zeta, k, ld);
   SM_TRY_CUDA(cudaGetLastError());
   return SM_OK;

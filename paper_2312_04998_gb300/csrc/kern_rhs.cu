@@ -91,17 +91,23 @@ __device__ __forceinline__ double dot_range(const uint32_t* __restrict__ ent, in
   return (s0 + s1) + (s2 + s3);
 }
 
-__global__ void __launch_bounds__(kCells * kChunks)
+// CRS gather of KC cells per block (cells as the fast axis) with KCH nonzero
+// chunks of about equal size, KC x KCH = 512 threads; a warp covers 32 / KC
+// chunks.  Rows split across chunks are summed in chunk order through shared
+// memory, so results do not depend on scheduling.
+template <int KC, int KCH>
+__global__ void __launch_bounds__(KC * KCH)
 rhs_crs_kernel(int n_s, int64_t C, const int* __restrict__ row_ptr, const uint32_t* __restrict__ ent,
                const int* __restrict__ row_id, const int* __restrict__ chunk_nz,
                const double* __restrict__ r, int64_t ldr, double* __restrict__ f, int64_t ld,
                const int* __restrict__ mask, int bit, const int* __restrict__ cact) {
-  if (cact && (int64_t)blockIdx.x * kCells >= *cact) return;      // no running cell in this block
-  __shared__ double part[kChunks][2][kCells];
-  __shared__ int carry_row[kChunks];
+  static_assert(KC * KCH == kCells * kChunks && 32 % KC == 0, "block shape");
+  if (cact && (int64_t)blockIdx.x * KC >= *cact) return;      // no running cell in this block
+  __shared__ double part[KCH][2][KC];
+  __shared__ int carry_row[KCH];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ch = warp * 2 + (lane >> 4), cl = lane & 15;
-  const int64_t c0 = (int64_t)blockIdx.x * kCells + cl;
+  const int ch = warp * (32 / KC) + lane / KC, cl = lane % KC;
+  const int64_t c0 = (int64_t)blockIdx.x * KC + cl;
   const bool live = c0 < C && (!mask || (mask[c0] & bit));
   if (mask && !__syncthreads_or(live)) return;
   const int64_t c = live ? c0 : 0;  // dead lanes read cell 0 and store nothing
@@ -114,12 +120,12 @@ rhs_crs_kernel(int n_s, int64_t C, const int* __restrict__ row_ptr, const uint32
     has_carry = true;
     carry = dot_range(ent, z0, min(__ldg(row_ptr + rc + 1), z1), r, ldr, c);
   }
-  // -2 marks an empty chunk (possible when nnz < kChunks): fix-ups skip it
+  // -2 marks an empty chunk (possible when nnz < KCH): fix-ups skip it
   if (cl == 0) carry_row[ch] = z0 == z1 ? -2 : (has_carry ? rc : -1);
   part[ch][0][cl] = carry;
   // rows owned by this chunk: row_ptr[row] in [z0, z1) (all rows for the last)
   const int r_first = lower_bound_i32(row_ptr, n_s, z0);
-  const int r_end = (ch == kChunks - 1) ? n_s : lower_bound_i32(row_ptr, n_s, z1);
+  const int r_end = (ch == KCH - 1) ? n_s : lower_bound_i32(row_ptr, n_s, z1);
   double tail = 0.0;
   int tail_row = -1;
   for (int row = r_first; row < r_end; ++row) {
@@ -136,7 +142,7 @@ rhs_crs_kernel(int n_s, int64_t C, const int* __restrict__ row_ptr, const uint32
   __syncthreads();
   if (tail_row >= 0) {
     double tot = part[ch][1][cl];
-    for (int w = ch + 1; w < kChunks; ++w) {
+    for (int w = ch + 1; w < KCH; ++w) {
       if (carry_row[w] == -2) continue;
       if (carry_row[w] != tail_row) break;
       tot += part[w][0][cl];
@@ -261,7 +267,7 @@ sm_status launch_rhs(const sm_net* net, int64_t C, const double* k, const double
   const unsigned groups = (unsigned)((C + kCells - 1) / kCells);
   if (F.fmt == SM_FMT_CRS) {
     if ((int)F.chunk_nz.size() != kChunks + 1) return SM_EINVAL;
-    rhs_crs_kernel<<<groups, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
+    rhs_crs_kernel<kCells, kChunks><<<groups, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
                                                        F.d_packed.as<uint32_t>(), F.d_aux.as<int>(),
                                                        F.d_chunk.as<int>(), scratch, ldr, f, ld,
                                                        nullptr, 0, nullptr);
@@ -287,14 +293,24 @@ sm_status launch_rhs_masked(const sm_net* net, int64_t C, const double* k, int64
   if (C == 0) return SM_OK;
   sm_status st = ensure_coef_table(net->device);
   if (st != SM_OK) return st;
-  const Format& F = net->integ;
+  const Format& F = net->integ_fmt[net->integ_order];
+  if (F.packed.empty()) return SM_EINVAL;
   dim3 grid((unsigned)((C + kRThreads - 1) / kRThreads), (unsigned)((net->n_r + kRChunk - 1) / kRChunk));
   reaction_rate_kernel<<<grid, kRThreads, 0, s>>>(net->n_r, C, net->d_reac.as<int2>(), k, ldk, y, ld,
                                                   scratch, ldr, mask, bit, cact);
   SM_TRY_CUDA(cudaGetLastError());
-  rhs_crs_kernel<<<(unsigned)((C + kCells - 1) / kCells), kCells * kChunks, 0, s>>>(
-      net->n_s, C, F.d_ptr.as<int>(), F.d_packed.as<uint32_t>(), F.d_aux.as<int>(), F.d_chunk.as<int>(),
-      scratch, ldr, f, ld, mask, bit, cact);
+  const int kc = net->integ_kc;
+  const unsigned nb = (unsigned)((C + kc - 1) / kc);
+  if (kc == 8) {
+    rhs_crs_kernel<8, 64><<<nb, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
+        F.d_packed.as<uint32_t>(), F.d_aux.as<int>(), F.d_chunk64.as<int>(), scratch, ldr, f, ld, mask, bit, cact);
+  } else if (kc == 32) {
+    rhs_crs_kernel<32, 16><<<nb, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
+        F.d_packed.as<uint32_t>(), F.d_aux.as<int>(), F.d_chunk16.as<int>(), scratch, ldr, f, ld, mask, bit, cact);
+  } else {
+    rhs_crs_kernel<16, 32><<<nb, kCells * kChunks, 0, s>>>(net->n_s, C, F.d_ptr.as<int>(),
+        F.d_packed.as<uint32_t>(), F.d_aux.as<int>(), F.d_chunk.as<int>(), scratch, ldr, f, ld, mask, bit, cact);
+  }
   SM_TRY_CUDA(cudaGetLastError());
   return SM_OK;
 }

@@ -665,14 +665,20 @@ sm_status build_format(const sm_net* net, int32_t fmt, int32_t order, int32_t C,
   // merge-style CRS kernel; row boundaries are found on the device).
   if (fmt == SM_FMT_CRS) {
     const int32_t nnz = (int32_t)f.idx.size();
-    const int32_t n_chunks = 32;  // must match the CRS kernel's chunks per CTA
-    for (int32_t c = 0; c <= n_chunks; ++c) f.chunk_nz.push_back((int32_t)((int64_t)nnz * c / n_chunks));
+    auto part = [&](int32_t n_chunks, std::vector<int32_t>& v) {
+      for (int32_t c = 0; c <= n_chunks; ++c) v.push_back((int32_t)((int64_t)nnz * c / n_chunks));
+    };
+    part(32, f.chunk_nz);    // must match the CRS kernels' chunks per CTA
+    part(64, f.chunk_nz64);
+    part(16, f.chunk_nz16);
   }
   // upload (skipped for host-only networks, device < 0)
   out->d_ptr.release();
   out->d_packed.release();
   out->d_aux.release();
   out->d_chunk.release();
+  out->d_chunk64.release();
+  out->d_chunk16.release();
   *out = std::move(f);
   Format& g = *out;
   if (net->device < 0) return SM_OK;
@@ -681,6 +687,10 @@ sm_status build_format(const sm_net* net, int32_t fmt, int32_t order, int32_t C,
   if ((st = g.d_packed.upload(g.packed.data(), g.packed.size() * 4)) != SM_OK) return st;
   if (!g.aux.empty() && (st = g.d_aux.upload(g.aux.data(), g.aux.size() * 4)) != SM_OK) return st;
   if (!g.chunk_nz.empty() && (st = g.d_chunk.upload(g.chunk_nz.data(), g.chunk_nz.size() * 4)) != SM_OK)
+    return st;
+  if (!g.chunk_nz64.empty() && (st = g.d_chunk64.upload(g.chunk_nz64.data(), g.chunk_nz64.size() * 4)) != SM_OK)
+    return st;
+  if (!g.chunk_nz16.empty() && (st = g.d_chunk16.upload(g.chunk_nz16.data(), g.chunk_nz16.size() * 4)) != SM_OK)
     return st;
   return SM_OK;
 }
@@ -810,5 +820,11 @@ sm_status net_upload(sm_net* net) {
   if ((st = lu.d_iperm.upload(lu.iperm.data(), lu.iperm.size() * 4)) != SM_OK) return st;
   int32_t zero = 0;
   if ((st = net->d_status.upload(&zero, 4)) != SM_OK) return st;
-  return build_format(net, SM_FMT_CRS, SM_ORDER_NONE, 1, 1, &net->integ);
+  return integ_format(net, SM_ORDER_NONE);
+}
+
+sm_status integ_format(sm_net* net, int32_t order) {
+  if (order < SM_ORDER_NONE || order > SM_ORDER_RCM) return SM_EINVAL;
+  if (!net->integ_fmt[order].packed.empty()) return SM_OK;
+  return build_format(net, SM_FMT_CRS, order, 1, 1, &net->integ_fmt[order]);
 }

@@ -6,9 +6,10 @@
 // (format x row order x SELL slice height C and sort window sigma) is built,
 // sm_rhs_eval is run on the caller's inputs and timed with CUDA events on the
 // caller's stream (one warm-up call, kTrials timed calls, median), and the
-// fastest candidate is left selected.  The kernels' own launch shapes (cells
-// per CTA, lanes per row) are compile-time constants of the kernels and are
-// not part of the search.  Results are cached for the process per (network
+// fastest candidate is left selected.  The integrator's own gather (a rate
+// pass and a masked CRS gather, run in every Newton iteration) is tuned in
+// the same call: CRS in each row order x 8, 16 or 32 cells per CTA (the
+// gather's block shape), timed the same way.  Results are cached for the process per (network
 // content hash, device name, batch-size bucket = C rounded up to a power of
 // two), so a later call with the same key selects the cached format without
 // timing anything.
@@ -112,6 +113,60 @@ sm_status time_rhs(sm_net* net, int64_t C, const double* k, const double* y, dou
   return SM_OK;
 }
 
+// Median time (ms) of kTrials integrator gathers (rate pass + masked CRS
+// gather, no mask) with the network's current integrator choice.
+sm_status time_integ(sm_net* net, int64_t C, const double* k, const double* y, double* f, int64_t ld,
+                     double* scratch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, double* ms_out) {
+  sm_status st = launch_rhs_masked(net, C, k, ld, y, f, ld, scratch, ld, nullptr, 0, nullptr, s);
+  if (st != SM_OK) return st;
+  std::vector<float> t(kTrials);
+  for (int i = 0; i < kTrials; ++i) {
+    SM_TRY_CUDA(cudaEventRecord(e0, s));
+    if ((st = launch_rhs_masked(net, C, k, ld, y, f, ld, scratch, ld, nullptr, 0, nullptr, s)) != SM_OK) return st;
+    SM_TRY_CUDA(cudaEventRecord(e1, s));
+    SM_TRY_CUDA(cudaEventSynchronize(e1));
+    SM_TRY_CUDA(cudaEventElapsedTime(&t[i], e0, e1));
+  }
+  std::sort(t.begin(), t.end());
+  *ms_out = t[kTrials / 2];
+  return SM_OK;
+}
+
+// The integrator's gather: CRS in each row order x 8 / 16 / 32 cells per CTA;
+// leaves the fastest selected and reports it in *out.
+sm_status tune_integ(sm_net* net, int64_t C, const double* k, const double* y, double* f, int64_t ld,
+                     cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, sm_tune_result* out) {
+  const int64_t ldr = (C + 31) / 32 * 32;
+  sm_status st = net->d_scratch.ensure(sizeof(double) * (size_t)net->n_r * (size_t)ldr);
+  if (st != SM_OK) return st;
+  const int32_t prev_order = net->integ_order, prev_kc = net->integ_kc;
+  double best = -1.0;
+  for (int32_t o : {SM_ORDER_NONE, SM_ORDER_NNZ, SM_ORDER_RCM}) {
+    if ((st = integ_format(net, o)) != SM_OK) break;
+    for (int32_t kc : {8, 16, 32}) {
+      net->integ_order = o;
+      net->integ_kc = kc;
+      double ms = 0.0;
+      if ((st = time_integ(net, C, k, y, f, ld, net->d_scratch.as<double>(), s, e0, e1, &ms)) != SM_OK) break;
+      if (best < 0.0 || ms < best) {
+        best = ms;
+        out->integ_order = o;
+        out->integ_cells_per_cta = kc;
+        out->integ_us = ms * 1e3;
+      }
+    }
+    if (st != SM_OK) break;
+  }
+  if (st != SM_OK) {
+    net->integ_order = prev_order;
+    net->integ_kc = prev_kc;
+    return st;
+  }
+  net->integ_order = out->integ_order;
+  net->integ_kc = out->integ_cells_per_cta;
+  return SM_OK;
+}
+
 }  // namespace
 
 extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, const double* d_y, double* d_f,
@@ -129,6 +184,9 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
       sm_tune_result r = it->second;
       sm_status st = net_select_format(net, r.fmt, r.order, r.sell_C, r.sell_sigma);
       if (st != SM_OK) return st;
+      if ((st = integ_format(net, r.integ_order)) != SM_OK) return st;
+      net->integ_order = r.integ_order;
+      net->integ_kc = r.integ_cells_per_cta;
       r.cached = 1;
       r.candidates = 0;   // nothing was timed by this call
       *out = r;
@@ -160,6 +218,7 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
       best.us = ms * 1e3;
     }
   }
+  if (st == SM_OK) st = tune_integ(net, C, d_k, d_y, d_f, ld, s, e0, e1, &best);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SM_OK) {
@@ -167,7 +226,7 @@ extern "C" sm_status sm_net_autotune(sm_net* net, int64_t C, const double* d_k, 
     net_select_format(net, prev.fmt, prev.order, prev.C, prev.sigma);
     return st;
   }
-  best.candidates = (int32_t)grid.size();
+  best.candidates = (int32_t)grid.size() + 9;
   best.cached = 0;
   if ((st = net_select_format(net, best.fmt, best.order, best.sell_C, best.sell_sigma)) != SM_OK) return st;
   {

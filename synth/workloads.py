@@ -22,6 +22,7 @@ class Workload:
     Av: object
     start: str            # "atomic" or "loguniform"
     t_end: float = 0.0
+    chi: float = 1.0      # FUV field scaling the photorates
     rtol: float = 1e-6
     atol: float = 1e-20
 
@@ -40,7 +41,22 @@ WORKLOADS = {
     "mixed_470x6000_c16384": Workload("mixed_470x6000_c16384", 470, 6000, 16384,
                                       (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0),
                                       "atomic", 1e6 * YEAR),
+    # the paper's PDR benchmark geometry (Section 3, model F2 of Roellig et al.
+    # 2007): a slab of 128 cells on a logarithmic A_V grid, n_H = 1e3, T = 50 K,
+    # FUV field chi = 1e5, atomic start, 30 Myr; the A_V grid is pdr_av()
+    "pdr_slab_470x6000_c128": Workload("pdr_slab_470x6000_c128", 470, 6000, 128,
+                                       50.0, 1e3, "pdr", "atomic", 30e6 * YEAR, chi=1e5),
 }
+
+PDR_AV_MIN, PDR_AV_MAX = 1e-3, 20.0
+
+
+def pdr_av(C):
+    """A_V of the slab's cells: the centres (in log A_V) of C cells evenly
+    spaced in log A_V between 1e-3 and 20, finest at the illuminated surface."""
+    import numpy as np
+    lo, hi = np.log10(PDR_AV_MIN), np.log10(PDR_AV_MAX)
+    return 10.0 ** (lo + (np.arange(C) + 0.5) * (hi - lo) / C)
 
 
 def make(name, cells=None):
@@ -50,7 +66,11 @@ def make(name, cells=None):
     w = WORKLOADS[name]
     C = w.cells if cells is None else cells
     desc = generate(NET_SEED, w.n_s, w.n_r)
-    T, nH, Av = _cells.conditions(CELL_SEED, C, w.T, w.nH, w.Av)
+    if w.Av == "pdr":
+        import numpy as np
+        T, nH, Av = np.full(C, float(w.T)), np.full(C, float(w.nH)), pdr_av(C)
+    else:
+        T, nH, Av = _cells.conditions(CELL_SEED, C, w.T, w.nH, w.Av)
     if w.start == "atomic":
         y0 = _cells.atomic_start(desc, C)
     else:

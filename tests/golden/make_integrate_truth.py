@@ -2,13 +2,17 @@
 the integrator tests: the oracle's BDF method at rtol 1e-10 / atol 1e-24 on
 seeded synthetic cells.  Calls only the oracle and the input generators.
 
-    python tests/golden/make_integrate_truth.py [small|large|strat|all]
+    python tests/golden/make_integrate_truth.py [small|large|strat|pdr|all]
 
 The "strat" case is a stiffness-stratified sample of the 16,384-cell
 mixed-precision workload (470 x 6000, T 10-1000 K, n_H 1e2-1e8, A_V 0-20,
 atomic start, 1e6 yr): every 128th of its cells is integrated by the oracle
 at rtol 1e-6, and the 32 cells at evenly spaced quantiles of those step
 counts are kept.
+
+The "pdr" case: 8 cells spread over the 128-cell PDR slab (the paper's
+benchmark geometry: n_H 1e3, T 50 K, FUV field 1e5 Draine fields on the
+photorates, A_V 1e-3 to 20 on a log grid, atomic start, 30 Myr).
 """
 import json
 import multiprocessing as mp
@@ -68,6 +72,35 @@ def _solve_all(name, rtol, atol, cells=None, C=None):
     return sorted(res, key=lambda r: order[r[0]])
 
 
+PDR_CELLS = [0, 18, 36, 54, 72, 90, 108, 127]
+
+
+def _pdr_one(args):
+    c, rtol, atol = args
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["pdr_slab_470x6000_c128"]
+    d, T, nH, Av, y0 = make(w.name)
+    k = ok.rate_coefficients(d, T[c:c + 1], nH[c:c + 1], Av[c:c + 1], chi=w.chi)[:, 0]
+    r = ob.integrate_cell(d, k, y0[:, c], w.t_end, ob.BDFOptions(rtol=rtol, atol=atol))
+    return c, r.y.tolist(), r.status, r.steps
+
+
+def make_pdr():
+    """integrate_truth_pdr.json: PDR_CELLS of the PDR slab at rtol 1e-10
+    (y) and at the tested rtol 1e-6 (y_rtol6), with both step counts."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(min(len(PDR_CELLS), os.cpu_count() or 1)) as pool:
+        r10 = pool.map(_pdr_one, [(c, 1e-10, 1e-24) for c in PDR_CELLS])
+        r6 = pool.map(_pdr_one, [(c, 1e-6, 1e-20) for c in PDR_CELLS])
+    out = {"source": "oracle BDF at rtol 1e-10, atol 1e-24 (make_integrate_truth.py)", "case": "pdr",
+           "workload": "pdr_slab_470x6000_c128", "cells": PDR_CELLS,
+           "y": [r[1] for r in r10], "status": [r[2] for r in r10], "steps": [r[3] for r in r10],
+           "y_rtol6": [r[1] for r in r6], "steps_rtol6": [r[3] for r in r6]}
+    with open(os.path.join(HERE, "integrate_truth_pdr.json"), "w") as fh:
+        json.dump(out, fh)
+
+
 def make_strat():
     """integrate_truth_strat.json: 32 cells of the 16,384-cell workload at
     evenly spaced quantiles of the oracle's rtol-1e-6 step count (drawn from
@@ -112,9 +145,11 @@ def make(name, only_rtol6=False):
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "all"
     only6 = "--rtol6-only" in sys.argv
-    for nm in (["small", "large", "strat"] if which == "all" else [which]):
+    for nm in (["small", "large", "strat", "pdr"] if which == "all" else [which]):
         if nm == "strat":
             make_strat()
+        elif nm == "pdr":
+            make_pdr()
         else:
             make(nm, only6)
         print("wrote", nm)

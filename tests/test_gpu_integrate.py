@@ -528,3 +528,81 @@ def test_step_replay_large_network(torch, B, strat_case, precision):
     _, wrms = replay_errors(d, k[:, sel], ys, tl, hl, ql, sample=12)
     assert len(wrms) >= 4 * 10
     assert wrms.max() <= 2.0, (wrms.max(), np.quantile(wrms, 0.9))
+
+
+@pytest.fixture(scope="module")
+def pdr_case():
+    """The PDR slab (128 cells, the paper's benchmark geometry with the
+    synthetic network) and the oracle's stored solutions for 8 of its cells."""
+    import json
+    import os
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["pdr_slab_470x6000_c128"]
+    d, T, nH, Av, y0 = make(w.name)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "integrate_truth_pdr.json")) as fh:
+        ref = json.load(fh)
+    return w, d, T, nH, Av, y0, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pdr_slab_matches_oracle(torch, B, pdr_case, precision):
+    """The whole 128-cell PDR slab (n_H 1e3, T 50 K, FUV field 1e5 on the
+    photorates, A_V 1e-3 to 20, 30 Myr): rate coefficients from
+    sm_rates_eval_chi against the oracle's (1e-13 relative), every cell
+    reaching t_end, and the 8 stored cells against the oracle's rtol-1e-10
+    solution with the bars of test_large_network_matches_oracle."""
+    w, d, T, nH, Av, y0, ref = pdr_case
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+    net = B.Network(d, 0)
+    pad = lambda v, fill: torch.tensor(np.concatenate([v, np.full(ld - C, fill)]), dtype=torch.float64,
+                                       device="cuda")
+    kd = torch.zeros((d.n_r, ld), dtype=torch.float64, device="cuda")
+    net.rates_eval_chi(pad(T, 100.0), pad(nH, 1.0), pad(Av, 0.0), pad(np.full(C, w.chi), 1.0), kd, C)
+    torch.cuda.synchronize()
+    k = kd.cpu().numpy()[:, :C]
+    kref = ok.rate_coefficients(d, T, nH, Av, chi=w.chi)
+    assert np.all(np.abs(k - kref) <= 1e-13 * np.abs(kref))
+    st = B.State(net, C, precision=precision)
+    yd = dev(torch, y0, ld)
+    stats = B.stats_tensor(C, "cuda")
+    assert st.integrate(kd, yd, w.t_end, C, stats) == B.SM_OK
+    torch.cuda.synchronize()
+    y, s = yd.cpu().numpy()[:, :C], B.stats_to_numpy(stats)
+    assert np.all(s["status"] == B.CELL_OK) and np.all(s["t"] == w.t_end)
+    cells = ref["cells"]
+    truth, yo = np.array(ref["y"]).T, np.array(ref["y_rtol6"]).T
+    e_o = np.maximum(cell_err(yo, truth), 1.0)
+    e_g = np.maximum(cell_err(y[:, cells], truth), 1.0)
+    assert e_g.max() <= 100.0, (e_g.max(), int(e_g.argmax()))
+    assert e_g.max() <= (1.5 if precision == "fp64" else 2.0) * e_o.max(), (e_g.max(), e_o.max())
+    assert np.median(e_g) <= 1.5 * np.median(e_o), (np.median(e_g), np.median(e_o))
+    steps_o = np.array(ref["steps_rtol6"])
+    assert np.all(np.abs(s["steps"][cells] - steps_o) <= 0.25 * steps_o + 10)
+
+
+@pytest.mark.parametrize("order", ["none", "nnz", "rcm"])
+@pytest.mark.parametrize("kc", [8, 16, 32])
+def test_integrator_gather_shapes(torch, B, moderate_case, order, kc):
+    """Every choice the autotuner can make for the integrator's gather (CRS
+    row order x cells per CTA) integrates the 40 moderate cells of the
+    32 x 180 network to the same solution as the default choice up to the
+    summation order of the right-hand side (which can move an accept /
+    reject decision: within 50 tolerance units of it) and within 100 units
+    of the oracle's rtol-1e-6 solution; a wrong gather is off by orders of
+    magnitude more."""
+    d, k, y0, t_end, ref, _ = moderate_case
+    C = y0.shape[1]
+    ld = B.pad_ld(C)
+    out = []
+    for choice in (("none", 16), (order, kc)):
+        net = B.Network(d, 0)
+        net.set_integ(*choice)
+        st = B.State(net, C)
+        yd = dev(torch, y0, ld)
+        assert st.integrate(dev(torch, k, ld), yd, t_end, C) == B.SM_OK
+        torch.cuda.synchronize()
+        out.append(yd.cpu().numpy()[:, :C])
+    assert cell_err(out[1], out[0]).max() <= 50.0
+    yo = np.stack([r.y for r in ref], axis=1)
+    assert cell_err(out[1], yo).max() <= 100.0

@@ -231,3 +231,6 @@ def test_autotune_selects_a_measured_format_and_keeps_parity(torch, B):
     net.sync()
     f = fd.cpu().numpy()[:, :C]
     assert np.all(np.abs(f - ok.rhs(d, k, y)) <= RTOL_F * ok.rhs_scale(d, k, y) + 1e-300)
+    # the integrator's gather was tuned too (3 row orders x 3 block shapes)
+    assert r["integ_cells_per_cta"] in (8, 16, 32) and r["integ_us"] > 0 and r["candidates"] >= 19
+    assert (r2["integ_order"], r2["integ_cells_per_cta"]) == (r["integ_order"], r["integ_cells_per_cta"])

@@ -94,6 +94,20 @@ def test_dissociative_recombination_rate_law():
     assert np.array_equal(kz, k)
 
 
+def test_fuv_field_scales_photorates_only():
+    """chi (the FUV field, Section 3) multiplies every photorate and nothing
+    else; chi = 1 is the default."""
+    d = sn.generate(2312, 470, 6000)
+    ph = d.rclass == 2
+    T, nH, Av = np.array([50.0, 50.0]), np.array([1e3, 1e3]), np.array([0.3, 7.0])
+    k1 = ok.rate_coefficients(d, T, nH, Av)
+    kc = ok.rate_coefficients(d, T, nH, Av, chi=np.array([1e5, 2.0]))
+    assert np.array_equal(ok.rate_coefficients(d, T, nH, Av, chi=1.0), k1)
+    assert np.allclose(kc[ph, 0], 1e5 * k1[ph, 0], rtol=1e-15)
+    assert np.allclose(kc[ph, 1], 2.0 * k1[ph, 1], rtol=1e-15)
+    assert np.array_equal(kc[~ph], k1[~ph])
+
+
 def test_rate_coefficient_log_linearity():
     """log k is linear in log(T/300) with slope beta, in 1/T with slope -gamma,
     and photorates fall as exp(-gamma A_V)."""
