@@ -484,16 +484,33 @@ def rhs_jac_grid(B, C, dev, peaks):
         net.set_format(*fmt)
         ms = med(lambda: net.rhs_eval(kd, yd, fd, C))
         out.append(row("rhs " + "/".join(str(x) for x in fmt), ms, info["rhs_bytes"], info["rhs_flops"]))
+    # the conventional right-hand side (generated per network, one explicit
+    # expression per species), timed the same way; same per-cell work units
+    conv = None
+    try:
+        from paper_2312_04998_gb300 import unrolled
+        t0 = time.time()
+        u = unrolled.Unrolled(d)
+        build_s = time.time() - t0
+        ms = med(lambda: u.rhs_eval(kd, yd, fd, C))
+        out.append(row("rhs conventional (generated)", ms, info["rhs_bytes"], info["rhs_flops"]))
+        conv = {"us": ms * 1e3, "kernels": u.n_kernels, "terms": u.n_terms, "build_s": build_s}
+    except Exception as exc:  # noqa: BLE001
+        conv = {"error": f"{type(exc).__name__}: {exc}"}
     net.set_format("crs", "none", 1, 1)
     ms = med(lambda: net.jac_eval(kd, yd, Jd, C))
     out.append(row("jac", ms, info["jac_bytes"], info["jac_flops"]))
     net.sync()
     net.close()
     best = max((r for r in out if r["kind"].startswith("rhs")), key=lambda r: r["binding_frac"])
+    crs = min((r for r in out if r["kind"].startswith("rhs crs")), key=lambda r: r["us"])
+    if conv and "us" in conv:
+        conv["crs_speedup"] = conv["us"] / crs["us"]
     return {"workload": "rhs_jac_470x6000_c4096", "cells": C, "l2": "flushed before every call",
             "rhs_bytes_per_cell": info["rhs_bytes"], "rhs_flops_per_cell": info["rhs_flops"],
             "jac_bytes_per_cell": info["jac_bytes"], "jac_flops_per_cell": info["jac_flops"],
             "peaks": peaks, "best_rhs": best["kind"], "best_rhs_binding_frac": best["binding_frac"],
+            "conventional": conv,
             "rows": out}
 
 

@@ -234,3 +234,25 @@ def test_autotune_selects_a_measured_format_and_keeps_parity(torch, B):
     # the integrator's gather was tuned too (3 row orders x 3 block shapes)
     assert r["integ_cells_per_cta"] in (8, 16, 32) and r["integ_us"] > 0 and r["candidates"] >= 19
     assert (r2["integ_order"], r2["integ_cells_per_cta"]) == (r["integ_order"], r["integ_cells_per_cta"])
+
+
+@pytest.mark.parametrize("shape", [(32, 180, 100), (470, 6000, 96)])
+def test_unrolled_conventional_rhs_matches_oracle(torch, B, shape):
+    """The generated conventional right-hand side (one explicit expression
+    per species, the pre-matrix algorithm of Section 3) against the oracle's
+    dense S R, with the bar of the stoichiometry-matrix kernels."""
+    from paper_2312_04998_gb300 import unrolled
+    n_s, n_r, C = shape
+    d = sn.generate(2312, n_s, n_r)
+    ld = B.pad_ld(C)
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e7), (0.0, 10.0))
+    y = sc.loguniform_abundances(d, 4998, C)
+    k = ok.rate_coefficients(d, T, nH, Av)
+    kd, yd = dev_mat(torch, k, ld, 0.0), dev_mat(torch, y, ld, 0.0)
+    fd = torch.full((d.n_s, ld), -1.0, dtype=torch.float64, device="cuda")
+    u = unrolled.Unrolled(d)
+    assert u.n_terms == sum(int(np.count_nonzero(on.stoichiometry(d)[i])) for i in range(d.n_s))
+    u.rhs_eval(kd, yd, fd, C)
+    torch.cuda.synchronize()
+    f = fd.cpu().numpy()[:, :C]
+    assert np.all(np.abs(f - ok.rhs(d, k, y)) <= RTOL_F * ok.rhs_scale(d, k, y) + 1e-300)
