@@ -134,15 +134,27 @@ def integrate_cell(desc, k, y0, t_end, opts: BDFOptions = BDFOptions(), S=None,
     if S is None:
         S = stoichiometry(desc)
     k = np.asarray(k, dtype=float)
-    n = desc.n_s
-    I = np.eye(n)
 
     def f(y):
         return S @ reaction_rates(desc, k, y)
 
+    def jac(y):
+        return jacobian(desc, k, y, S)
+
     y0 = np.array(y0, dtype=float)
+    if not np.all(np.isfinite(k)):
+        return CellResult(y=y0.copy(), t=0.0, status=STATUS_NAN)
+    return integrate_system(f, jac, y0, t_end, opts, record, history)
+
+
+def integrate_system(f, jac, y0, t_end, opts: BDFOptions = BDFOptions(), record=False,
+                     history=None) -> CellResult:
+    """The method above for any system dy/dt = f(y) with Jacobian jac(y)
+    (dense n x n), from t = 0 to t_end."""
+    y0 = np.array(y0, dtype=float)
+    I = np.eye(y0.shape[0])
     res = CellResult(y=y0.copy(), t=0.0)
-    if not np.all(np.isfinite(y0)) or not np.all(np.isfinite(k)):
+    if not np.all(np.isfinite(y0)):
         res.status = STATUS_NAN
         return res
     Y, T = [y0.copy()], [0.0]
@@ -185,7 +197,7 @@ def integrate_cell(desc, k, y0, t_end, opts: BDFOptions = BDFOptions(), S=None,
         w = 1.0 / (opts.rtol * np.abs(Y[0]) + opts.atol)
         refresh = need_J or j_age >= opts.j_age_max or abs(gamma / gamma_J - 1.0) > opts.gamma_tol
         if refresh:
-            J = jacobian(desc, k, y_pred, S)
+            J = jac(y_pred)
             lu = sla.lu_factor(I - gamma * J)
             gamma_J, j_age, crate, need_J = gamma, 0, 1.0, False
             res.jac_evals += 1
