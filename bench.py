@@ -94,6 +94,8 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-pdr", action="store_true", help="skip the PDR-slab simulation")
+    p.add_argument("--thermal-cells", type=int, default=4096,
+                   help="cells of the coupled-temperature leg (0 skips it)")
     p.add_argument("--no-tune", action="store_true", help="integrate with the default gather, untuned")
     p.add_argument("--mixed-cells", type=int, default=16384,
                    help="cells of the FP64 vs mixed comparison (0 = skip)")
@@ -103,7 +105,7 @@ def args_():
                    help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
     p.add_argument("--budget-s", type=float, default=1200.0,
                    help="auxiliary measurements start only while the run is younger than this")
-    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe", "pdr"],
+    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe", "pdr", "thermal"],
                    help="run one auxiliary measurement alone and print it")
     p.add_argument("--phases", action="store_true",
                    help="refresh-kernel cycles per phase over one integration (phase-clock build)")
@@ -560,6 +562,51 @@ def pdr_slab(B, dev, precisions=("mixed", "fp64")):
     return out
 
 
+def thermal_leg(B, dev, cells=4096, precisions=("mixed", "fp64")):
+    """Coupled gas temperature (NEXT row: the energy equation as one more BDF
+    component, k'(T) re-evaluated inside every Newton iteration): the first
+    `cells` cells of the coupled-temperature workload integrated to 1e6 yr
+    as one whole simulation timed with CUDA events (sm_state_set_cells +
+    sm_integrate, after an untimed run that captures the graphs)."""
+    import numpy as np
+    import torch
+    from synth.workloads import WORKLOADS, make_thermal
+    w = WORKLOADS["thermal_470x6000_c16384"]
+    d, th, nH, Av, z0 = make_thermal(w.name, cells=cells)
+    C = z0.shape[1]
+    ld = B.pad_ld(C)
+    net = B.Network(d, dev.index or 0)
+    net.set_thermal(th)
+    vec = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    nHd, Avd = vec(nH), vec(Av)
+    z0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
+    z0d[:, :C] = vec(z0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": w.name, "cells": C, "t_end_yr": w.t_end / YEAR}
+    for prec in precisions:
+        st = B.State(net, C, precision=prec)
+        st.set_cells(nHd, Avd, None, C)
+        stats = B.stats_tensor(C, dev)
+        zd = z0d.clone()
+
+        def run():
+            zd.copy_(z0d)
+            return st.integrate(None, zd, w.t_end, C, stats)
+
+        run()
+        code, ms = timed(run, stream)
+        s = B.stats_to_numpy(stats)
+        T1 = zd[th.t_index, :C].cpu().numpy()
+        out[prec] = {"seconds": ms * 1e-3, "cell_steps_per_s": float(s["steps"].sum()) / (ms * 1e-3),
+                     "steps_per_cell": float(s["steps"].mean()), "max_steps": int(s["steps"].max()),
+                     "newton_per_step": float(s["newton_iters"].sum()) / max(float(s["steps"].sum()), 1.0),
+                     "cells_ok": int((s["status"] == 0).sum()), "status": int(code),
+                     "T_final_K": {"min": float(T1.min()), "median": float(np.median(T1)), "max": float(T1.max())}}
+        st.close()
+    net.close()
+    return out
+
+
 def peaks_(B, dev):
     """HBM: the measured copy bandwidth (MEASURED_PEAKS.json); FP64 / FP32:
     unit counts x clock, with this run's FMA-probe rates beside them."""
@@ -730,7 +777,8 @@ def main():
         fn = {"rhs": lambda: rhs_jac_grid(B, a.rhs_cells, dev, peaks_(B, dev)),
               "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
               "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
-              "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev)}[a.only]
+              "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev),
+              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells)}[a.only]
         if rank == 0:
             print(json.dumps(fn()))
         return
@@ -869,6 +917,7 @@ def main():
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
     pdr = None if a.no_pdr else aux(pdr_slab, B, dev)
+    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells)
     cpu = None if a.no_cpu else aux(cpu_baseline, t_end)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -889,7 +938,7 @@ def main():
                   "cells_ok": int((s["status"] == 0).sum())},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "pdr_slab": pdr, "peaks": peaks,
+        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "pdr_slab": pdr, "thermal": therm, "peaks": peaks,
         "wall_s": time.time() - t_start,
     }
     print(json.dumps(out))

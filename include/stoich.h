@@ -382,6 +382,54 @@ sm_status sm_state_load(sm_state* st, const void* host, size_t bytes, void* stre
 sm_status sm_state_timing(const sm_state* st, int64_t* launches, double* ms, int64_t* timed);
 sm_status sm_state_timing_reset(sm_state* st);
 
+/* ---- Coupled gas temperature ---------------------------------------------
+ * The paper holds T fixed inside a chemistry step and updates the energy
+ * outside the chemical solver (Section 5).  A network given a temperature
+ * slot by sm_net_set_thermal integrates T as one more component of the same
+ * implicit BDF system.  Slot t is a species with no atoms, no charge and no
+ * reactions whose value is the gas temperature in K; with x_tot the sum of
+ * the other components (electrons included) and f = S R(k'(T), x) (Eq. 7),
+ *   3/2 x_tot dT/dt = heat - n_H sum_i x_i L_i exp(-E_i / T)
+ *                     - lam n_H (T - T_dust) - 3/2 T sum_{i != t} f_i,
+ * i.e. the thermal energy 3/2 T x_tot per H nucleus gains a constant heating,
+ * loses two-level line cooling and gas-grain exchange, and follows the
+ * particle number.  The two-body and dissociative-recombination
+ * coefficients k' (the T-dependent classes) are re-evaluated from the state's
+ * T before every right-hand side; the cosmic-ray and photo ones once, at
+ * sm_state_init.  The Newton matrix keeps the species block's sparse LU and
+ * adds T by block elimination: per refresh one more substitution
+ * (z = M^-1 (-gamma dF/dT)) and a scalar Schur complement, per Newton
+ * iteration one dot product and one update; the result is the solution of
+ * the full (n_s) x (n_s) system with T eliminated last.
+ *
+ * sm_net_set_thermal: th = NULL turns the mode off.  L and E are host arrays
+ * of n_s values (copied): L_i >= 0 in K cm^3 s^-1 (0: not a coolant), E_i > 0
+ * in K where L_i > 0.  heat (K s^-1 per H nucleus), lam (cm^3 s^-1), T_dust
+ * (K) and zeta (s^-1, the cosmic-ray rate of the rate laws) >= 0.  SM_EINVAL
+ * if slot t has atoms or charge or appears in a reaction.  States created
+ * from the network afterwards take a copy of the setting; a thermal state
+ * needs opts.record_steps = 0 (SM_ENOTSUP otherwise: no adjoint), cannot be
+ * saved or loaded (SM_ENOTSUP), and needs the cells' conditions from
+ * sm_state_set_cells before sm_state_init / sm_integrate; its d_k arguments
+ * are ignored and may be NULL. */
+typedef struct {
+    int32_t t_index;       /* species slot holding T (K)                            */
+    double heat;           /* constant heating per H nucleus, K s^-1                */
+    double lam;            /* gas-grain coupling coefficient, cm^3 s^-1             */
+    double T_dust;         /* dust temperature, K                                   */
+    double zeta;           /* cosmic-ray ionisation rate of the rate laws, s^-1     */
+    const double* L;       /* host [n_s]: line-cooling coefficients, K cm^3 s^-1    */
+    const double* E;       /* host [n_s]: excitation temperatures, K                */
+} sm_thermal;
+sm_status sm_net_set_thermal(sm_net* net, const sm_thermal* th);
+
+/* Per-cell conditions of a thermal state: n_H (cm^-3), A_V and the FUV
+ * field chi (d_chi may be NULL: 1) for cells 0..C-1, device arrays of C
+ * doubles, copied on `stream` into the state (C <= capacity).  SM_ENOTSUP on
+ * a state without a temperature slot. */
+sm_status sm_state_set_cells(sm_state* st, int64_t C, const double* d_nH, const double* d_Av,
+                             const double* d_chi, void* stream);
+
 /* ---- Sensitivities: discrete adjoint of the BDF integration -----------------
  * The paper integrates the network but computes no derivatives; these calls
  * are the library's addition.  They differentiate the frozen-step map of the

@@ -57,6 +57,11 @@ class TuneResult_c(ct.Structure):
                 ("integ_order", ct.c_int32), ("integ_cells_per_cta", ct.c_int32), ("integ_us", ct.c_double)]
 
 
+class Thermal_c(ct.Structure):
+    _fields_ = [("t_index", ct.c_int32), ("heat", ct.c_double), ("lam", ct.c_double), ("T_dust", ct.c_double),
+                ("zeta", ct.c_double), ("L", ct.c_void_p), ("E", ct.c_void_p)]
+
+
 class Opts_c(ct.Structure):
     _fields_ = [("rtol", ct.c_double), ("atol", ct.c_double), ("gamma_tol", ct.c_double),
                 ("newton_tol", ct.c_double), ("eta_max", ct.c_double), ("eta_keep", ct.c_double),
@@ -88,6 +93,9 @@ _SIGS = [
     ("sm_net_set_format", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]),
     ("sm_net_get_info", ct.c_int32, [ct.c_void_p, ct.POINTER(NetInfo_c)]),
     ("sm_net_set_integ", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.c_int32]),
+    ("sm_net_set_thermal", ct.c_int32, [ct.c_void_p, ct.POINTER(Thermal_c)]),
+    ("sm_state_set_cells", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                        ct.c_void_p]),
     ("sm_net_autotune", ct.c_int32, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                      ct.c_int64, ct.c_int32, ct.c_void_p, ct.POINTER(TuneResult_c)]),
     ("sm_net_export_size", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_size_t)]),
@@ -279,6 +287,18 @@ class Network:
         """The integrator's gather: CRS row order and cells per CTA (8, 16, 32)."""
         _check(lib().sm_net_set_integ(self.h, ORDER[order], int(cells_per_cta)), "sm_net_set_integ")
 
+    def set_thermal(self, th):
+        """Couple the gas temperature (sm_net_set_thermal); th has t_index, L,
+        E, heat, lam, T_dust and zeta (None turns it off)."""
+        if th is None:
+            _check(lib().sm_net_set_thermal(self.h, None), "sm_net_set_thermal")
+            return
+        L = np.ascontiguousarray(th.L, dtype=np.float64)
+        E = np.ascontiguousarray(th.E, dtype=np.float64)
+        c = Thermal_c(int(th.t_index), float(th.heat), float(th.lam), float(th.T_dust), float(th.zeta),
+                      L.ctypes.data, E.ctypes.data)
+        _check(lib().sm_net_set_thermal(self.h, ct.byref(c)), "sm_net_set_thermal")
+
     def rhs_eval(self, k, y, f, C):
         ld = self._ld(k, y, f)
         _check(lib().sm_rhs_eval(self.h, int(C), _dptr(k), _dptr(y), _dptr(f), int(ld),
@@ -367,14 +387,23 @@ class State:
         _check(lib().sm_state_bytes(self.h, ct.byref(n)), "sm_state_bytes")
         return n.value
 
+    def set_cells(self, nH, Av, chi=None, C=None):
+        """Cell conditions of a thermal state (device FP64 arrays of >= C)."""
+        C = nH.shape[0] if C is None else C
+        _check(lib().sm_state_set_cells(self.h, int(C), _dptr(nH), _dptr(Av),
+                                        _dptr(chi) if chi is not None else None, _stream(nH.device)),
+               "sm_state_set_cells")
+
     def integrate(self, k, y, t_end, C=None, stats=None, allow_partial=True):
         """Integrate C cells from t = 0 to t_end; y (device [n_s][ld]) is
         overwritten.  stats: optional device uint8 tensor of C*48 bytes.
-        Returns the status code (SM_OK or SM_EPARTIAL)."""
+        k may be None for a thermal state.  Returns the status code (SM_OK
+        or SM_EPARTIAL)."""
         C = y.shape[1] if C is None else C
-        ld = self.net._ld(k, y)
+        ld = self.net._ld(k, y) if k is not None else self.net._ld(y)
         self.generation += 1
-        code = lib().sm_integrate(self.h, int(C), _dptr(k), _dptr(y), int(ld), float(t_end),
+        code = lib().sm_integrate(self.h, int(C), _dptr(k) if k is not None else None, _dptr(y), int(ld),
+                                  float(t_end),
                                   _dptr(stats) if stats is not None else None, _stream(y.device))
         if code == SM_EPARTIAL and allow_partial:
             return code
@@ -384,11 +413,17 @@ class State:
     def init(self, k, y, t_end, C=None):
         C = y.shape[1] if C is None else C
         self.generation += 1
-        _check(lib().sm_state_init(self.h, int(C), _dptr(k), _dptr(y), int(self.net._ld(k, y)),
+        ld = self.net._ld(k, y) if k is not None else self.net._ld(y)
+        _check(lib().sm_state_init(self.h, int(C), _dptr(k) if k is not None else None, _dptr(y), int(ld),
                                    float(t_end), _stream(y.device)), "sm_state_init")
 
-    def step(self, k, attempts):
-        _check(lib().sm_step_bdf(self.h, _dptr(k), int(k.stride(0)), int(attempts), _stream(k.device)),
+    def step(self, k, attempts, device=None):
+        """attempts BDF attempts; k may be None for a thermal state (then
+        device, default the network's, selects the stream)."""
+        import torch
+        dev = k.device if k is not None else torch.device("cuda", self.net.device if device is None else device)
+        _check(lib().sm_step_bdf(self.h, _dptr(k) if k is not None else None,
+                                 int(k.stride(0)) if k is not None else 32, int(attempts), _stream(dev)),
                "sm_step_bdf")
 
     def read(self, y=None, stats=None):

@@ -1,6 +1,7 @@
 // extern "C" entry points of stoich.h: argument checks, device selection and
 // dispatch to the host builders and kernel launchers.  No entry point aborts,
 // traps or exits; failures come back as sm_status codes.
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <new>
@@ -179,6 +180,41 @@ sm_status sm_net_set_format(sm_net* net, int32_t fmt, int32_t order, int32_t sel
     return net_select_format(net, fmt, order, sell_C, sell_sigma);
   }
   return net_select_format(net, fmt, order, sell_C, sell_sigma);
+}
+
+sm_status sm_net_set_thermal(sm_net* net, const sm_thermal* th) {
+  if (!net) return SM_EINVAL;
+  if (!th) {
+    net->th_t = -1;
+    net->th_L.clear();
+    net->th_E.clear();
+    return SM_OK;
+  }
+  const int32_t t = th->t_index, n = net->n_s, ne = net->n_elem + 1;
+  if (t < 0 || t >= n || !th->L || !th->E) return SM_EINVAL;
+  auto ok = [](double v) { return std::isfinite(v) && v >= 0.0; };
+  if (!ok(th->heat) || !ok(th->lam) || !ok(th->T_dust) || !ok(th->zeta)) return SM_EINVAL;
+  for (int32_t e = 0; e < ne; ++e)
+    if (net->comp[(size_t)t * ne + e] != 0) return SM_EINVAL;   // no atoms, no charge
+  for (int32_t v : net->reac)
+    if (v == t) return SM_EINVAL;                                // in no reaction
+  for (int32_t v : net->prod)
+    if (v == t) return SM_EINVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!ok(th->L[i])) return SM_EINVAL;
+    if (th->L[i] > 0.0 && !(std::isfinite(th->E[i]) && th->E[i] > 0.0)) return SM_EINVAL;
+  }
+  net->th_L.assign(th->L, th->L + n);
+  net->th_E.assign(th->E, th->E + n);
+  net->th_L[t] = 0.0;
+  for (int32_t i = 0; i < n; ++i)
+    if (net->th_L[i] == 0.0) net->th_E[i] = 1.0;
+  net->th_heat = th->heat;
+  net->th_lam = th->lam;
+  net->th_Td = th->T_dust;
+  net->th_zeta = th->zeta;
+  net->th_t = t;
+  return SM_OK;
 }
 
 sm_status sm_net_set_integ(sm_net* net, int32_t order, int32_t cells_per_cta) {

@@ -90,6 +90,16 @@ struct Dev {
   const int4* jdesc;     // per Jacobian entry {t0, t1, jrc, row << 16 | col}
   const int* jlong;      // entries with more than kJLong terms
   int n_jlong;
+  // coupled temperature (therm = 1, see sm_net_set_thermal): row t_idx of
+  // every state vector holds T; k' of the T-dependent reactions is
+  // recomputed from it (into kslot) before every right-hand side
+  int therm, t_idx, n_cool, bpad;
+  double th_heat, th_lam, th_Td, th_zeta;
+  const RatePar* rpar;
+  const double *th_L, *th_E, *th_dn;   // [n] cooling coefficients, [n] excitation temperatures, [n_r] net particle change
+  const int* th_cool;                  // [n_cool] the coolant species
+  const double *c_nH, *c_Av, *c_chi;   // [ld] cell conditions, cell order
+  double *bz, *bgv, *bs;               // per cell (cell order): z, gamma_J v ([ld][bpad]) and the Schur complement ([ld])
 };
 
 __device__ __forceinline__ double& V(double* a, const Dev& d, int s, int64_t c) {
@@ -152,10 +162,17 @@ __global__ void init_copy_kernel(Dev d, const double* __restrict__ yin, int64_t 
     V(Y0, d, s, c) = v;
     ok = ok && isfinite(v);
   }
-  for (int j = 0; j < d.n_r; ++j) {
-    const double kv = k[(int64_t)j * ldk + c];
-    ok = ok && isfinite(kv);
-    if (d.kslot) d.kslot[(int64_t)j * d.ld + c] = kv;
+  if (k) {
+    for (int j = 0; j < d.n_r; ++j) {
+      const double kv = k[(int64_t)j * ldk + c];
+      ok = ok && isfinite(kv);
+      if (d.kslot) d.kslot[(int64_t)j * d.ld + c] = kv;
+    }
+  }
+  if (d.therm) {
+    const int64_t oc = c;
+    ok = ok && V(Y0, d, d.t_idx, c) > 0.0 && isfinite(d.c_nH[oc]) && d.c_nH[oc] > 0.0 && isfinite(d.c_Av[oc]) &&
+         isfinite(d.c_chi[oc]);
   }
   d.slot_cell[c] = (int)c;
   d.status[c] = ok ? SM_CELL_RUNNING : SM_CELL_NAN;
@@ -1192,9 +1209,11 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, i
   T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)wi * xs;
   const double a0 = d.alpha[c], h = d.h[c];
   const double inv_a0 = 1.0 / a0;
+  double rT = 0.0;   // the temperature row's residual, kept in FP64
   for (int s = lane; s < n; s += 32) {
     const int64_t o = (int64_t)s * d.ld + c;
     double b = -(a0 * d.y[o] + d.psi[o] - h * d.f[o]) * inv_a0;
+    if (s == d.t_idx) rT = b;
     if (d.mixed) b *= d.wf[o];
     x[__ldg(d.iperm + s)] = T(b);
   }
@@ -1203,11 +1222,31 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, i
   else lu_substitute<T>(d, static_cast<const T*>(d.lu) + c * d.lu_stride, x, lane);
   const double gamma = d.gam[c], gJ = d.gam_J[c];
   const double scale = gamma != gJ ? 2.0 / (1.0 + gamma / gJ) : 1.0;
+  // coupled temperature: T eliminated last (see th_border_kernel); the
+  // species block's solution a0 becomes a0 - z bT, and T moves by bT
+  double bT = 0.0;
+  const double* bz = nullptr;
+  if (d.therm) {
+    const int64_t oc = d.slot_cell[c];
+    const double* bgv = d.bgv + oc * d.bpad;
+    bz = d.bz + oc * d.bpad;
+    double dot = 0.0;
+    for (int s = lane; s < n; s += 32) {
+      if (s == d.t_idx) continue;
+      double a = (double)x[__ldg(d.iperm + s)];
+      if (d.mixed) a /= d.wf[(int64_t)s * d.ld + c];
+      dot = fma(bgv[s], a, dot);
+    }
+    dot = warp_sum(dot);
+    rT = __shfl_sync(0xffffffffu, rT, d.t_idx & 31);
+    bT = (rT + dot) / d.bs[oc];
+  }
   double acc = 0.0;
   for (int s = lane; s < n; s += 32) {
     const int64_t o = (int64_t)s * d.ld + c;
     double del = (double)x[__ldg(d.iperm + s)];
     if (d.mixed) del /= d.wf[o];
+    if (bz) del = s == d.t_idx ? bT : fma(-bz[s], bT, del);
     del *= scale;
     d.y[o] += del;
     const double v = del * d.w[o];
@@ -1233,6 +1272,179 @@ __global__ void __launch_bounds__(32 * kSolveWarps) solve_update_kernel(Dev d, i
     d.m_it[c] = m + 1;
     d.newton_iters[c] += 1;
     if (conv || fail) d.flags[c] = (d.flags[c] & ~F_NEWTON) | (conv ? F_CONV : F_FAILED);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coupled temperature (sm_net_set_thermal)
+//
+// T is component t_idx of the state.  Before every right-hand side the
+// T-dependent coefficients (two-body, dissociative recombination) are
+// recomputed from the slot's T into kslot; after the CRS gather of the
+// chemical rows, th_energy_kernel sets the temperature row
+//   f_t = (heat - n_H sum_i x_i L_i exp(-E_i/T) - lam n_H (T - T_dust)
+//          - 3/2 T sum_{i != t} f_i) / (3/2 x_tot);
+// after a refresh, th_border_kernel adds T to the Newton matrix by block
+// elimination.
+// ---------------------------------------------------------------------------
+constexpr int kThRatesChunk = 64;
+constexpr int kBorderWarps = 2;
+
+// k' in slot order from the slots' temperatures Trow[slot] (a row of a
+// state vector).  init = 1 (start of an integration): every class, every
+// slot below C; else the T-dependent classes of the slots in Newton
+// iterations.
+__global__ void __launch_bounds__(128) th_rates_kernel(Dev d, const double* __restrict__ Trow, int init) {
+  const int64_t c = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (c >= d.C) return;
+  if (!init && ((d.compact && c >= d.counters[kCAct]) || !(d.flags[c] & F_NEWTON))) return;
+  const int j0 = blockIdx.y * kThRatesChunk, j1 = min(d.n_r, j0 + kThRatesChunk);
+  const int64_t oc = d.slot_cell[c];
+  const double T = Trow[c], nH = d.c_nH[oc];
+  const double lt = log(T * (1.0 / 300.0)), it = 1.0 / T;
+  for (int j = j0; j < j1; ++j) {
+    const RatePar p = d.rpar[j];   // (log alpha | alpha, beta, gamma, class)
+    const int cls = (int)p.w;
+    double v;
+    if (cls == SM_TWO_BODY || cls == SM_DISS_RECOMB) v = exp(fma(p.y, lt, p.x) - p.z * it) * nH;
+    else if (!init) continue;
+    else if (cls == SM_COSMIC_RAY) v = p.x * d.th_zeta;
+    else v = d.c_chi[oc] * p.x * exp(-p.z * d.c_Av[oc]);
+    d.kslot[(int64_t)j * d.ld + c] = v;
+  }
+}
+
+// The temperature row f[t] from y and the chemical rows of f, for the slots
+// in Newton iterations (init = 1: every slot below C).
+__global__ void __launch_bounds__(128) th_energy_kernel(Dev d, const double* __restrict__ y, double* __restrict__ f,
+                                                        int init) {
+  const int64_t c = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  if (c >= d.C) return;
+  if (!init && ((d.compact && c >= d.counters[kCAct]) || !(d.flags[c] & F_NEWTON))) return;
+  const int t = d.t_idx;
+  const double T = y[(int64_t)t * d.ld + c];
+  double xt = 0.0, F = 0.0;
+  for (int s = 0; s < d.n; ++s) {
+    if (s == t) continue;
+    xt += y[(int64_t)s * d.ld + c];
+    F += f[(int64_t)s * d.ld + c];
+  }
+  const int64_t oc = d.slot_cell[c];
+  const double nH = d.c_nH[oc];
+  double line = 0.0;
+  for (int q = 0; q < d.n_cool; ++q) {
+    const int i = __ldg(d.th_cool + q);
+    line = fma(y[(int64_t)i * d.ld + c], d.th_L[i] * exp(-d.th_E[i] / T), line);
+  }
+  f[(int64_t)t * d.ld + c] = (d.th_heat - nH * line - d.th_lam * nH * (T - d.th_Td) - 1.5 * T * F) / (1.5 * xt);
+}
+
+// After a refresh, per refreshed cell (warp per cell): the temperature
+// border of its Newton matrix.  With u = dF/dT (F the chemical rows),
+// v = d f_t / dx and w = d f_t / dT at the predicted state, the full matrix
+// is  [M, -gJ u; -gJ v^T, 1 - gJ w]  (M the species block the refresh
+// factorised, gJ = gamma_J).  Eliminating T last leaves
+//   z = M^-1 (-gJ u),   s = 1 - gJ w + gJ v.z,
+// and the Newton correction of a residual (r, r_T) is (a0 - z b, b) with
+// a0 = M^-1 r and b = (r_T + gJ v.a0) / s (solve_update_kernel).  The
+// sums over the chemical rows come from the reactions: sum_i S_ij = dn_j,
+// so sum_i f_i = sum_j dn_j R_j and sum_i J_il = sum_j dn_j dR_j/dx_l.
+template <class T>
+__global__ void __launch_bounds__(32 * kBorderWarps) th_border_kernel(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int n = d.n, t = d.t_idx, xs = (n + 3) / 4 * 4;
+  double* u = reinterpret_cast<double*>(smem_raw) + (int64_t)wi * 3 * xs;   // dF/dT
+  double* vv = u + xs;                                                      // sum_j dn_j dR_j/dx_l
+  double* ys = vv + xs;                                                     // the predicted state
+  T* x = reinterpret_cast<T*>(reinterpret_cast<double*>(smem_raw) + (int64_t)kBorderWarps * 3 * xs) +
+         (int64_t)wi * xs;
+  const int count = d.counters[0];
+  for (int e = blockIdx.x * kBorderWarps + wi; e < count; e += gridDim.x * kBorderWarps) {
+    const int64_t c = d.list[e];
+    const int64_t oc = d.slot_cell[c];
+    for (int s = lane; s < n; s += 32) {
+      u[s] = 0.0;
+      vv[s] = 0.0;
+      ys[s] = d.ypred[(int64_t)s * d.ld + c];
+    }
+    __syncwarp();
+    const double Tc = ys[t], it = 1.0 / Tc;
+    double F = 0.0, U = 0.0;
+    for (int j = lane; j < d.n_r; j += 32) {
+      const int2 rc = __ldg(d.reac + j);
+      const double kv = d.kslot[(int64_t)j * d.ld + c];
+      const double ya = ys[rc.x], yb = rc.y >= 0 ? ys[rc.y] : 1.0;
+      const double R = kv * ya * yb;
+      const RatePar p = d.rpar[j];
+      const int cls = (int)p.w;
+      const double g = (cls == SM_TWO_BODY || cls == SM_DISS_RECOMB) ? (p.y + p.z * it) * it : 0.0;  // d ln k'/dT
+      const double dn = __ldg(d.th_dn + j);
+      F = fma(dn, R, F);
+      if (g != 0.0) {
+        const double Rg = R * g;
+        U = fma(dn, Rg, U);
+        for (int q = __ldg(d.sc_ptr + j); q < __ldg(d.sc_ptr + j + 1); ++q) {
+          const uint32_t ent = __ldg(d.sc_ent + q);
+          atomicAdd(&u[ent & 0xFFFFFF], (double)(int8_t)(ent >> 24) * Rg);
+        }
+      }
+      if (dn != 0.0) {
+        if (rc.y < 0) {
+          atomicAdd(&vv[rc.x], dn * kv);
+        } else if (rc.x == rc.y) {
+          atomicAdd(&vv[rc.x], dn * 2.0 * kv * ya);
+        } else {
+          atomicAdd(&vv[rc.x], dn * kv * yb);
+          atomicAdd(&vv[rc.y], dn * kv * ya);
+        }
+      }
+    }
+    F = warp_sum(F);
+    U = warp_sum(U);
+    __syncwarp();
+    const double nH = d.c_nH[oc];
+    double xt = 0.0, line = 0.0, dline = 0.0;
+    for (int s = lane; s < n; s += 32)
+      if (s != t) xt += ys[s];
+    for (int q = lane; q < d.n_cool; q += 32) {
+      const int i = __ldg(d.th_cool + q);
+      const double cl = d.th_L[i] * exp(-d.th_E[i] * it);
+      line = fma(ys[i], cl, line);
+      dline = fma(ys[i] * cl, d.th_E[i] * it * it, dline);
+    }
+    xt = warp_sum(xt);
+    line = warp_sum(line);
+    dline = warp_sum(dline);
+    const double i15x = 1.0 / (1.5 * xt);
+    const double fT = (d.th_heat - nH * line - d.th_lam * nH * (Tc - d.th_Td) - 1.5 * Tc * F) * i15x;
+    const double w = (-nH * dline - d.th_lam * nH - 1.5 * F - 1.5 * Tc * U) * i15x;
+    const double gJ = d.gam_J[c];
+    for (int s = lane; s < n; s += 32) {
+      double b = s == t ? 0.0 : -gJ * u[s];
+      if (d.mixed) b *= d.wf[(int64_t)s * d.ld + c];
+      x[__ldg(d.iperm + s)] = T(b);
+    }
+    __syncwarp();
+    lu_substitute_packed<T>(d, static_cast<const T*>(d.lup) + oc * d.lup_stride, x, lane);
+    double* bz = d.bz + oc * d.bpad;
+    double* bgv = d.bgv + oc * d.bpad;
+    double vz = 0.0;
+    for (int s = lane; s < n; s += 32) {
+      double z = 0.0, v = 0.0;
+      if (s != t) {
+        z = (double)x[__ldg(d.iperm + s)];
+        if (d.mixed) z /= d.wf[(int64_t)s * d.ld + c];
+        const double cl = d.th_L[s] > 0.0 ? d.th_L[s] * exp(-d.th_E[s] * it) : 0.0;
+        v = (-nH * cl - 1.5 * Tc * vv[s]) * i15x - fT / xt;
+      }
+      bz[s] = z;
+      bgv[s] = gJ * v;
+      vz = fma(v, z, vz);
+    }
+    vz = warp_sum(vz);
+    if (lane == 0) d.bs[oc] = 1.0 - gJ * w + gJ * vz;
+    __syncwarp();
   }
 }
 
@@ -1842,6 +2054,17 @@ __global__ void replay_out_kernel(Dev d, AdjDev a, double* __restrict__ yout, in
 
 }  // namespace
 
+// Cell conditions of a thermal state (chi = 1 where none is given).
+static __global__ void th_cells_kernel(Dev d, int64_t C, const double* __restrict__ nH, const double* __restrict__ Av,
+                                const double* __restrict__ chi) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double* cond = const_cast<double*>(d.c_nH);
+  cond[c] = nH[c];
+  cond[d.ld + c] = Av[c];
+  cond[2 * d.ld + c] = chi ? chi[c] : 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1852,6 +2075,9 @@ struct sm_state {
   double t_end = 0.0;
   Dev d{};
   DevArray scal_d, scal_i, vec, lu, lup, list, counters, scratch, rec_d, rec_i, kslot, cpt;
+  DevArray th_par, th_cool, cond, bord;   // coupled temperature: parameters, coolants, cell conditions, border
+  int64_t cells_set = 0;                  // cells whose conditions sm_state_set_cells copied
+  size_t border_smem = 0;
   const double* kslot_src = nullptr;   // the caller's k the slot-ordered copy was taken from
   DevArray adj_d, adj_i, adj_lu;   // sm_adjoint workspace, grown on demand
   cudaStream_t s = nullptr, s2 = nullptr;          // s2: second half of the Newton rounds
@@ -1925,6 +2151,10 @@ void free_state(sm_state* st) {
   st->lup.release();
   st->kslot.release();
   st->cpt.release();
+  st->th_par.release();
+  st->th_cool.release();
+  st->cond.release();
+  st->bord.release();
   st->list.release();
   st->counters.release();
   st->scratch.release();
@@ -2000,7 +2230,18 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
     k = d.kslot;   // the rate coefficients in slot order
     ldk = d.ld;
   }
+  const dim3 th_grid(blocks(d.C, 128), (unsigned)((d.n_r + kThRatesChunk - 1) / kThRatesChunk));
+  if (d.therm) {
+    // k'(T) at the predicted state, for the refresh and the first Newton round
+    th_rates_kernel<<<th_grid, 128, 0, s>>>(d, d.ypred + (int64_t)d.t_idx * d.ld, 0);
+    st->launches += 1;
+  }
   refresh_kernel<T><<<st->refresh_ctas, kRefreshThreads, st->plan.bytes, s>>>(d, k, ldk, st->plan);
+  if (d.therm) {
+    const unsigned nb = (unsigned)std::min<int64_t>(blocks(d.C, kBorderWarps), 152LL * 16);
+    th_border_kernel<T><<<nb, 32 * kBorderWarps, st->border_smem, s>>>(d);
+    st->launches += 1;
+  }
   if ((r = time_mark(st, SM_TIME_REFRESH, false, s)) != SM_OK) return r;
   const size_t smem = sizeof(T) * (size_t)kSolveWarps * ((d.n + 3) / 4 * 4);
   // Newton rounds.  Unless the RHS or solve class is being timed, the cells
@@ -2021,9 +2262,17 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
     Dev dh = shift_cells(d, c0, cn);
     for (int m = 0; m < d.newton_max; ++m) {
       if ((r = time_mark(st, SM_TIME_RHS, true, hs)) != SM_OK) return r;
+      if (d.therm && m > 0) {
+        th_rates_kernel<<<dim3(blocks(cn, 128), th_grid.y), 128, 0, hs>>>(dh, dh.y + (int64_t)d.t_idx * d.ld, 0);
+        st->launches += 1;
+      }
       r = launch_rhs_masked(net, cn, k + c0, ldk, dh.y, dh.f, d.ld, st->scratch.as<double>() + c0, d.ld,
                             dh.flags, F_NEWTON, d.compact ? d.counters + kCAct : nullptr, hs);
       if (r != SM_OK) return r;
+      if (d.therm) {
+        th_energy_kernel<<<blocks(cn, 128), 128, 0, hs>>>(dh, dh.y, dh.f, 0);
+        st->launches += 1;
+      }
       if ((r = time_mark(st, SM_TIME_RHS, false, hs)) != SM_OK) return r;
       if ((r = time_mark(st, SM_TIME_SOLVE, true, hs)) != SM_OK) return r;
       solve_update_kernel<T><<<blocks(cn, kSolveWarps), 32 * kSolveWarps, smem, hs>>>(dh, F_NEWTON, F_NEWTON);
@@ -2373,6 +2622,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   sm_opts_default(&o);
   if (opts) o = *opts;
   if (!opts_ok(o)) return SM_EINVAL;
+  if (net->th_t >= 0 && o.record_steps > 0) return SM_ENOTSUP;   // no adjoint of the coupled system
   Scope scope(net->device);
   if (!scope.ok) return SM_ECUDA;
   sm_state* st = new (std::nothrow) sm_state();
@@ -2551,6 +2801,57 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.lu_cta = d.record ? 0 : 1;
   if ((r = st->lu.ensure(esz * (size_t)d.lu_stride * (d.lu_cta ? st->refresh_ctas : C))) != SM_OK) return fail(r);
   d.lu = st->lu.p;
+  // coupled temperature: a copy of the network's setting
+  d.therm = 0;
+  d.t_idx = -1;
+  if (net->th_t >= 0) {
+    d.therm = 1;
+    d.t_idx = net->th_t;
+    d.th_heat = net->th_heat;
+    d.th_lam = net->th_lam;
+    d.th_Td = net->th_Td;
+    d.th_zeta = net->th_zeta;
+    d.rpar = net->d_rate.as<RatePar>();
+    std::vector<double> par(2 * (size_t)n + net->n_r);
+    std::vector<int> cool;
+    for (int i = 0; i < n; ++i) {
+      par[i] = net->th_L[i];
+      par[n + i] = net->th_E[i];
+      if (net->th_L[i] > 0.0) cool.push_back(i);
+    }
+    for (int j = 0; j < net->n_r; ++j) {   // sum_i S_ij: products minus reactants
+      int dn = 0;
+      for (int q = 0; q < 2; ++q) dn -= net->reac[2 * j + q] >= 0 ? 1 : 0;
+      for (int q = 0; q < 4; ++q) dn += net->prod[4 * j + q] >= 0 ? 1 : 0;
+      par[2 * n + j] = dn;
+    }
+    if ((r = st->th_par.upload(par.data(), par.size() * sizeof(double))) != SM_OK) return fail(r);
+    d.th_L = st->th_par.as<double>();
+    d.th_E = d.th_L + n;
+    d.th_dn = d.th_L + 2 * n;
+    d.n_cool = (int)cool.size();
+    if (!cool.empty() && (r = st->th_cool.upload(cool.data(), cool.size() * sizeof(int))) != SM_OK) return fail(r);
+    d.th_cool = st->th_cool.as<int>();
+    if ((r = st->cond.ensure(sizeof(double) * 3 * (size_t)ld)) != SM_OK) return fail(r);
+    d.c_nH = st->cond.as<double>();
+    d.c_Av = d.c_nH + ld;
+    d.c_chi = d.c_nH + 2 * ld;
+    d.bpad = (n + 3) / 4 * 4;
+    if ((r = st->bord.ensure(sizeof(double) * (2 * (size_t)d.bpad + 1) * ld)) != SM_OK) return fail(r);
+    d.bz = st->bord.as<double>();
+    d.bgv = d.bz + (int64_t)d.bpad * ld;
+    d.bs = d.bgv + (int64_t)d.bpad * ld;
+    const int xs = (n + 3) / 4 * 4;
+    st->border_smem = (size_t)kBorderWarps * xs * (3 * sizeof(double) + esz);
+    if (st->border_smem > 48 * 1024) {
+      const cudaError_t e =
+          d.mixed ? cudaFuncSetAttribute(th_border_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)st->border_smem)
+                  : cudaFuncSetAttribute(th_border_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)st->border_smem);
+      if (e != cudaSuccess) return fail(SM_ECUDA);
+    }
+  }
   SM_TRY_CUDA(cudaMemset(st->scal_i.p, 0, st->scal_i.bytes));
   *out = st;
   return SM_OK;
@@ -2566,7 +2867,8 @@ sm_status sm_state_free(sm_state* st) {
 
 sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
   if (!st || !bytes) return SM_EINVAL;
-  *bytes = st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->lup.bytes + st->kslot.bytes +
+  *bytes = st->th_par.bytes + st->th_cool.bytes + st->cond.bytes + st->bord.bytes +
+           st->scal_d.bytes + st->scal_i.bytes + st->vec.bytes + st->lu.bytes + st->lup.bytes + st->kslot.bytes +
            st->cpt.bytes + st->list.bytes +
            st->counters.bytes + st->scratch.bytes + st->rec_d.bytes + st->rec_i.bytes + st->adj_d.bytes + st->adj_i.bytes +
            st->adj_lu.bytes;
@@ -2575,7 +2877,9 @@ sm_status sm_state_bytes(const sm_state* st, size_t* bytes) {
 
 sm_status sm_state_init(sm_state* st, int64_t C, const double* d_k, const double* d_y, int64_t ld,
                         double t_end, void* stream) {
-  if (!st || C < 1 || C > st->cap || !ld_ok(C, ld) || !d_k || !d_y || !(t_end > 0.0)) return SM_EINVAL;
+  const bool therm = st && st->d.therm;
+  if (!st || C < 1 || C > st->cap || !ld_ok(C, ld) || (!d_k && !therm) || !d_y || !(t_end > 0.0)) return SM_EINVAL;
+  if (therm && st->cells_set < C) return SM_EINVAL;   // sm_state_set_cells first
   Scope scope(st->net->device);
   if (!scope.ok) return SM_ECUDA;
   sm_status r;
@@ -2585,12 +2889,25 @@ sm_status sm_state_init(sm_state* st, int64_t C, const double* d_k, const double
   Dev& d = st->d;
   d.C = C;
   d.t_end = t_end;
+  if (therm) d_k = nullptr;
   init_copy_kernel<<<blocks(C, 128), 128, 0, st->s>>>(d, d_y, ld, d_k, ld);
   SM_TRY_CUDA(cudaGetLastError());
   st->kslot_src = d_k;
-  r = launch_rhs_masked(st->net, C, d_k, ld, d.Y, d.f0, d.ld, st->scratch.as<double>(), d.ld, d.flags,
-                        F_NEWTON, nullptr, st->s);
+  if (therm) {
+    // every rate coefficient from the initial T (slot order = cell order here)
+    th_rates_kernel<<<dim3(blocks(C, 128), (unsigned)((d.n_r + kThRatesChunk - 1) / kThRatesChunk)), 128, 0,
+                      st->s>>>(d, d.Y + (int64_t)d.t_idx * d.ld, 1);
+    SM_TRY_CUDA(cudaGetLastError());
+    st->launches += 1;
+  }
+  r = launch_rhs_masked(st->net, C, therm ? d.kslot : d_k, therm ? d.ld : ld, d.Y, d.f0, d.ld,
+                        st->scratch.as<double>(), d.ld, d.flags, F_NEWTON, nullptr, st->s);
   if (r != SM_OK) return r;
+  if (therm) {
+    th_energy_kernel<<<blocks(C, 128), 128, 0, st->s>>>(d, d.Y, d.f0, 1);
+    SM_TRY_CUDA(cudaGetLastError());
+    st->launches += 1;
+  }
   init_finish_kernel<<<blocks(C, 128), 128, 0, st->s>>>(d);
   SM_TRY_CUDA(cudaGetLastError());
   st->launches += 4;
@@ -2598,12 +2915,16 @@ sm_status sm_state_init(sm_state* st, int64_t C, const double* d_k, const double
 }
 
 sm_status sm_step_bdf(sm_state* st, const double* d_k, int64_t ld, int32_t attempts, void* stream) {
-  if (!st || !d_k || st->C < 1 || !ld_ok(st->C, ld) || attempts < 0) return SM_EINVAL;
+  if (!st || (!d_k && !st->d.therm) || st->C < 1 || (!st->d.therm && !ld_ok(st->C, ld)) || attempts < 0)
+    return SM_EINVAL;
   Scope scope(st->net->device);
   if (!scope.ok) return SM_ECUDA;
   sm_status r;
   if ((r = join_in(st, stream)) != SM_OK) return r;
-  if (st->d.kslot && st->kslot_src != d_k) {
+  if (st->d.therm) {
+    d_k = nullptr;   // k' comes from the state's temperatures
+    ld = st->d.ld;
+  } else if (st->d.kslot && st->kslot_src != d_k) {
     kslot_gather_kernel<<<blocks(st->C, 128), 128, 0, st->s>>>(st->d, d_k, ld);
     SM_TRY_CUDA(cudaGetLastError());
     st->launches += 1;
@@ -2626,6 +2947,21 @@ sm_status sm_state_read(sm_state* st, double* d_y, int64_t ld, sm_cell_stats* d_
     st->launches += 1;
   }
   if (h_running && (r = running_count(st, h_running)) != SM_OK) return r;
+  return join_out(st, stream);
+}
+
+sm_status sm_state_set_cells(sm_state* st, int64_t C, const double* d_nH, const double* d_Av, const double* d_chi,
+                             void* stream) {
+  if (!st || C < 1 || C > st->cap || !d_nH || !d_Av) return SM_EINVAL;
+  if (!st->d.therm) return SM_ENOTSUP;
+  Scope scope(st->net->device);
+  if (!scope.ok) return SM_ECUDA;
+  sm_status r;
+  if ((r = join_in(st, stream)) != SM_OK) return r;
+  th_cells_kernel<<<blocks(C, 128), 128, 0, st->s>>>(st->d, C, d_nH, d_Av, d_chi);
+  SM_TRY_CUDA(cudaGetLastError());
+  st->launches += 1;
+  st->cells_set = C;
   return join_out(st, stream);
 }
 
@@ -2759,6 +3095,7 @@ void image_sizes(const sm_state* st, int with_factors, uint64_t* b) {
 extern "C" sm_status sm_state_save(sm_state* st, int32_t with_factors, void* host, size_t bytes,
                                    size_t* needed, void* stream) {
   if (!st || !needed) return SM_EINVAL;
+  if (st->d.therm) return SM_ENOTSUP;
   uint64_t b[5];
   image_sizes(st, with_factors, b);
   const size_t total = sizeof(StateImage) + b[0] + b[1] + b[2] + b[3] + b[4];
@@ -2809,6 +3146,7 @@ extern "C" sm_status sm_state_save(sm_state* st, int32_t with_factors, void* hos
 
 extern "C" sm_status sm_state_load(sm_state* st, const void* host, size_t bytes, void* stream) {
   if (!st || !host || bytes < sizeof(StateImage)) return SM_EINVAL;
+  if (st->d.therm) return SM_ENOTSUP;
   StateImage im;
   std::memcpy(&im, host, sizeof im);
   uint64_t b[5];

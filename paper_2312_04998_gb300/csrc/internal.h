@@ -151,6 +151,12 @@ struct sm_net {
   DevArray d_status;      // int32 device status word
   DevArray d_scratch;     // reaction-rate scratch for rhs_eval
   sm_net_info info{};
+  // Coupled temperature (sm_net_set_thermal; states copy it at creation):
+  // slot th_t holds T (-1: off), line-cooling coefficients and excitation
+  // temperatures per species, and the constant parameters.
+  int32_t th_t = -1;
+  double th_heat = 0.0, th_lam = 0.0, th_Td = 0.0, th_zeta = 0.0;
+  std::vector<double> th_L, th_E;
 };
 
 // Host-side builders (net_build.cpp).

@@ -46,6 +46,12 @@ WORKLOADS = {
     # FUV field chi = 1e5, atomic start, 30 Myr; the A_V grid is pdr_av()
     "pdr_slab_470x6000_c128": Workload("pdr_slab_470x6000_c128", 470, 6000, 128,
                                        50.0, 1e3, "pdr", "atomic", 30e6 * YEAR, chi=1e5),
+    # coupled gas temperature (the energy equation of synth/thermal.py as one
+    # more state component): the mixed-precision workload's cells, each
+    # starting at its drawn T, the temperature slot appended to the network
+    "thermal_470x6000_c16384": Workload("thermal_470x6000_c16384", 470, 6000, 16384,
+                                        (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0),
+                                        "atomic", 1e6 * YEAR),
 }
 
 PDR_AV_MIN, PDR_AV_MAX = 1e-3, 20.0
@@ -57,6 +63,15 @@ def pdr_av(C):
     import numpy as np
     lo, hi = np.log10(PDR_AV_MIN), np.log10(PDR_AV_MAX)
     return 10.0 ** (lo + (np.arange(C) + 0.5) * (hi - lo) / C)
+
+
+def make_thermal(name, cells=None):
+    """(desc with the temperature slot, thermal parameters, nH, Av, z0) for a
+    coupled-temperature workload; z0's slot row holds the cells' initial T."""
+    from . import thermal as _th
+    desc, T, nH, Av, y0 = make(name, cells)
+    d_t = _th.with_temperature(desc)
+    return d_t, _th.thermal_params(d_t), nH, Av, _th.thermal_start(d_t, y0, T)
 
 
 def make(name, cells=None):

@@ -2,7 +2,7 @@
 the integrator tests: the oracle's BDF method at rtol 1e-10 / atol 1e-24 on
 seeded synthetic cells.  Calls only the oracle and the input generators.
 
-    python tests/golden/make_integrate_truth.py [small|large|strat|pdr|all]
+    python tests/golden/make_integrate_truth.py [small|large|strat|pdr|thermal_small|thermal_large|all]
 
 The "strat" case is a stiffness-stratified sample of the 16,384-cell
 mixed-precision workload (470 x 6000, T 10-1000 K, n_H 1e2-1e8, A_V 0-20,
@@ -13,6 +13,9 @@ counts are kept.
 The "pdr" case: 8 cells spread over the 128-cell PDR slab (the paper's
 benchmark geometry: n_H 1e3, T 50 K, FUV field 1e5 Draine fields on the
 photorates, A_V 1e-3 to 20 on a log grid, atomic start, 30 Myr).
+
+The "thermal_*" cases integrate the coupled-temperature system
+(oracle/thermal.py) from each cell's drawn T.
 """
 import json
 import multiprocessing as mp
@@ -101,6 +104,59 @@ def make_pdr():
         json.dump(out, fh)
 
 
+THERMAL_SMALL_CELLS = list(range(16))
+THERMAL_POOL = 256      # the large thermal case samples the first 256 cells ...
+THERMAL_LARGE_N = 8     # ... at evenly spaced quantiles of n_H
+
+
+def thermal_inputs(n_s, n_r, cells):
+    """(desc with the temperature slot, thermal parameters, nH, Av, z0) of the
+    coupled-temperature cases: the "strat" ranges (T 10-1000 K, n_H 1e2-1e8,
+    A_V 0-20), atomic start at each cell's drawn T."""
+    from synth import thermal as sth
+    d = sth.with_temperature(sn.generate(2312, n_s, n_r))
+    cells = np.asarray(cells)
+    T, nH, Av = sc.conditions(4998, int(cells.max()) + 1, (10.0, 1000.0), (1e2, 1e8), (0.0, 20.0))
+    T, nH, Av = T[cells], nH[cells], Av[cells]
+    return d, sth.thermal_params(d), nH, Av, sth.thermal_start(d, sc.atomic_start(d, len(cells)), T)
+
+
+def thermal_large_cells():
+    _, _, nH, _, _ = thermal_inputs(32, 180, np.arange(THERMAL_POOL))
+    order = np.argsort(nH, kind="stable")
+    return sorted(int(order[int((i + 0.5) * THERMAL_POOL / THERMAL_LARGE_N)]) for i in range(THERMAL_LARGE_N))
+
+
+def _thermal_one(args):
+    n_s, n_r, c, rtol, atol = args
+    from oracle import thermal as oth
+    d, th, nH, Av, z0 = thermal_inputs(n_s, n_r, [c])
+    r = oth.integrate_cell(d, th, (float(nH[0]), float(Av[0]), 1.0), z0[:, 0], 1e6 * YEAR,
+                           ob.BDFOptions(rtol=rtol, atol=atol))
+    return c, r.y.tolist(), r.status, r.steps
+
+
+def make_thermal(name):
+    """integrate_truth_<name>.json for the coupled-temperature cases
+    (thermal_small: 32 x 180, cells 0-15; thermal_large: 470 x 6000, 8 cells
+    at quantiles of n_H among the first 256), to 1e6 yr: rtol-1e-10 (y) and
+    rtol-1e-6 (y_rtol6) oracle solutions with their step counts."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    n_s, n_r = (32, 180) if name == "thermal_small" else (470, 6000)
+    cells = THERMAL_SMALL_CELLS if name == "thermal_small" else thermal_large_cells()
+    with mp.get_context("spawn").Pool(min(2 * len(cells), os.cpu_count() or 1)) as pool:
+        r10 = pool.map_async(_thermal_one, [(n_s, n_r, c, 1e-10, 1e-24) for c in cells])
+        r6 = pool.map_async(_thermal_one, [(n_s, n_r, c, 1e-6, 1e-20) for c in cells])
+        r10, r6 = r10.get(), r6.get()
+    out = {"source": "oracle BDF at rtol 1e-10, atol 1e-24 (make_integrate_truth.py)", "case": name,
+           "n_s": n_s, "n_r": n_r, "cells": list(cells), "t_end": 1e6 * YEAR,
+           "y": [r[1] for r in r10], "status": [r[2] for r in r10], "steps": [r[3] for r in r10],
+           "y_rtol6": [r[1] for r in r6], "steps_rtol6": [r[3] for r in r6]}
+    with open(os.path.join(HERE, f"integrate_truth_{name}.json"), "w") as fh:
+        json.dump(out, fh)
+
+
 def make_strat():
     """integrate_truth_strat.json: 32 cells of the 16,384-cell workload at
     evenly spaced quantiles of the oracle's rtol-1e-6 step count (drawn from
@@ -145,11 +201,13 @@ def make(name, only_rtol6=False):
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "all"
     only6 = "--rtol6-only" in sys.argv
-    for nm in (["small", "large", "strat", "pdr"] if which == "all" else [which]):
+    for nm in (["small", "large", "strat", "pdr", "thermal_small", "thermal_large"] if which == "all" else [which]):
         if nm == "strat":
             make_strat()
         elif nm == "pdr":
             make_pdr()
+        elif nm.startswith("thermal"):
+            make_thermal(nm)
         else:
             make(nm, only6)
         print("wrote", nm)
