@@ -562,7 +562,7 @@ def pdr_slab(B, dev, precisions=("mixed", "fp64")):
     return out
 
 
-def thermal_leg(B, dev, cells=4096, precisions=("mixed", "fp64")):
+def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
     """Coupled gas temperature (NEXT row: the energy equation as one more BDF
     component, k'(T) re-evaluated inside every Newton iteration): the first
     `cells` cells of the coupled-temperature workload integrated to 1e6 yr

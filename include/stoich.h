@@ -300,6 +300,9 @@ typedef struct {
     int32_t record_steps;     /* > 0: record up to this many accepted steps per cell
                                  (times, sizes, orders) and the step history every
                                  SM_CHECKPOINT_EVERY steps, for sm_adjoint         */
+    int32_t refresh_ctas_per_sm; /* refresh CTAs resident per SM: 0 = as many as
+                                 fit (default); fewer CTAs keep fewer working
+                                 matrices in flight (L2 footprint)            */
 } sm_opts;
 
 /* Accepted steps between stored states of the recorded forward run. */

@@ -68,7 +68,7 @@ class Opts_c(ct.Structure):
                 ("q_max", ct.c_int32), ("max_steps", ct.c_int32), ("j_age_max", ct.c_int32),
                 ("newton_max", ct.c_int32), ("max_conv_fails", ct.c_int32), ("precision", ct.c_int32),
                 ("use_graph", ct.c_int32), ("attempts_per_sync", ct.c_int32),
-                ("timing_kind", ct.c_int32), ("record_steps", ct.c_int32)]
+                ("timing_kind", ct.c_int32), ("record_steps", ct.c_int32), ("refresh_ctas_per_sm", ct.c_int32)]
 
 
 CELL_STATS_DTYPE = np.dtype([("status", np.int32), ("steps", np.int32), ("rejects", np.int32),

@@ -2115,6 +2115,7 @@ extern "C" void sm_opts_default(sm_opts* o) {
   o->attempts_per_sync = 8;
   o->timing_kind = SM_TIME_NONE;
   o->record_steps = 0;
+  o->refresh_ctas_per_sm = 0;
 }
 
 namespace {
@@ -2137,7 +2138,8 @@ bool opts_ok(const sm_opts& o) {
          o.newton_max >= 1 && o.newton_max <= 8 && o.max_conv_fails >= 1 &&
          (o.precision == SM_PREC_FP64 || o.precision == SM_PREC_MIXED || o.precision == SM_PREC_TF32) &&
          o.attempts_per_sync >= 1 &&
-         o.timing_kind >= SM_TIME_NONE && o.timing_kind <= SM_TIME_FINISH && o.record_steps >= 0;
+         o.timing_kind >= SM_TIME_NONE && o.timing_kind <= SM_TIME_FINISH && o.record_steps >= 0 &&
+         o.refresh_ctas_per_sm >= 0;
 }
 
 void free_state(sm_state* st) {
@@ -2795,6 +2797,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refresh_kernel<double>, kRefreshThreads, rsm);
   }
+  if (o.refresh_ctas_per_sm > 0) per_sm = std::min(per_sm, (int)o.refresh_ctas_per_sm);
   st->refresh_ctas = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   // dense working matrices of the refresh: one per refresh CTA, except in
   // recording states, whose replays keep dense factors per cell
