@@ -411,7 +411,7 @@ sm_status sm_state_timing_reset(sm_state* st);
  * (K) and zeta (s^-1, the cosmic-ray rate of the rate laws) >= 0.  SM_EINVAL
  * if slot t has atoms or charge or appears in a reaction.  States created
  * from the network afterwards take a copy of the setting; a thermal state
- * needs opts.record_steps = 0 (SM_ENOTSUP otherwise: no adjoint), cannot be
+ * records steps (sm_state_steps) but has no adjoint or replay and cannot be
  * saved or loaded (SM_ENOTSUP), and needs the cells' conditions from
  * sm_state_set_cells before sm_state_init / sm_integrate; its d_k arguments
  * are ignored and may be NULL. */

@@ -311,14 +311,20 @@ def solve_step(desc, k, hist_y, hist_t, t_new, h, S=None, tol=1e-14, max_iter=30
     if S is None:
         S = stoichiometry(desc)
     k = np.asarray(k, dtype=float)
+    return solve_step_system(lambda y: S @ reaction_rates(desc, k, y), lambda y: jacobian(desc, k, y, S),
+                             hist_y, hist_t, t_new, h, tol, max_iter, y_start)
+
+
+def solve_step_system(f, jac, hist_y, hist_t, t_new, h, tol=1e-14, max_iter=30, y_start=None):
+    """solve_step for any system dy/dt = f(y) with Jacobian jac(y)."""
     q = len(hist_y)
     alpha = bdf_alphas([t_new] + list(hist_t[:q]), h)
     psi = sum(alpha[i] * np.asarray(hist_y[i - 1], dtype=float) for i in range(1, q + 1))
     y = np.array(hist_y[0] if y_start is None else y_start, dtype=float)
-    I = np.eye(desc.n_s)
+    I = np.eye(y.shape[0])
     for _ in range(max_iter):
-        G = alpha[0] * y + psi - h * (S @ reaction_rates(desc, k, y))
-        delta = np.linalg.solve(alpha[0] * I - h * jacobian(desc, k, y, S), -G)
+        G = alpha[0] * y + psi - h * f(y)
+        delta = np.linalg.solve(alpha[0] * I - h * jac(y), -G)
         y = y + delta
         if np.all(np.abs(delta) <= tol * np.abs(y)):
             break

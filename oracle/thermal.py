@@ -32,7 +32,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .bdf import BDFOptions, CellResult, STATUS_NAN, integrate_system
+from .bdf import BDFOptions, CellResult, STATUS_NAN, integrate_system, solve_step_system
 from .kinetics import jacobian as chem_jacobian
 from .kinetics import reaction_rates
 from .network import stoichiometry
@@ -135,3 +135,12 @@ def integrate(desc, th, nH, Av, chi, z0, t_end, opts: BDFOptions = BDFOptions(),
     cells = range(C) if cells is None else cells
     return [integrate_cell(desc, th, (float(nH[c]), float(Av[c]), float(chi[c])), z0[:, c], t_end, opts, S)
             for c in cells]
+
+
+def solve_step(desc, th, cell, hist_y, hist_t, t_new, h, S=None, tol=1e-14, max_iter=30, y_start=None):
+    """Exact solution of one implicit BDF step of the coupled system (see
+    oracle/bdf.py solve_step), given its history newest first."""
+    if S is None:
+        S = stoichiometry(desc)
+    return solve_step_system(lambda z: rhs(desc, th, cell, z, S), lambda z: jacobian(desc, th, cell, z, S),
+                             hist_y, hist_t, t_new, h, tol, max_iter, y_start)

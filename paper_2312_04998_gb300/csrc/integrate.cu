@@ -2251,8 +2251,8 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   // (FP64-pipe bound) of one half overlaps the substitution (bandwidth
   // bound) of the other.
   // (not with compaction: the running cells are then all in the first half)
-  const bool split = !d.compact && st->opts.timing_kind != SM_TIME_RHS && st->opts.timing_kind != SM_TIME_SOLVE &&
-                     d.C >= 2 * kSplitMin;
+  const bool split = !d.compact && !d.therm && st->opts.timing_kind != SM_TIME_RHS &&
+                     st->opts.timing_kind != SM_TIME_SOLVE && d.C >= 2 * kSplitMin;
   const int64_t ch = split ? (d.C / 2 + 31) / 32 * 32 : d.C;
   if (split) {
     SM_TRY_CUDA(cudaEventRecord(st->ev_fork, s));
@@ -2624,7 +2624,6 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   sm_opts_default(&o);
   if (opts) o = *opts;
   if (!opts_ok(o)) return SM_EINVAL;
-  if (net->th_t >= 0 && o.record_steps > 0) return SM_ENOTSUP;   // no adjoint of the coupled system
   Scope scope(net->device);
   if (!scope.ok) return SM_ECUDA;
   sm_state* st = new (std::nothrow) sm_state();
@@ -2679,8 +2678,12 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   // compaction of running cells in states that record no steps (the
   // adjoint's records are indexed by cell)
   d.compact = o.record_steps > 0 ? 0 : 1;
-  if (d.compact) {
+  // slot-ordered rate coefficients: with compaction, and always with a
+  // coupled temperature (its k'(T) is rewritten before every right-hand side)
+  if (d.compact || net->th_t >= 0) {
     if ((r = st->kslot.ensure(sizeof(double) * (size_t)net->n_r * ld)) != SM_OK) return fail(r);
+  }
+  if (d.compact) {
     if ((r = st->cpt.ensure(sizeof(int) * 2 * (size_t)ld)) != SM_OK) return fail(r);
   }
   if ((r = st->scratch.ensure(sizeof(double) * (size_t)net->n_r * ld)) != SM_OK) return fail(r);
@@ -2698,7 +2701,7 @@ sm_status sm_state_create(const sm_net* net, int64_t C, const sm_opts* opts, sm_
   d.f0 = d.f + vs; d.eprev = d.f0 + vs; d.w = d.eprev + vs; d.wf = d.w + vs;
   d.list = st->list.as<int>();
   d.counters = st->counters.as<int>();
-  d.kslot = d.compact ? st->kslot.as<double>() : nullptr;
+  d.kslot = st->kslot.p ? st->kslot.as<double>() : nullptr;
   d.holes = d.compact ? st->cpt.as<int>() : nullptr;
   d.runners = d.compact ? st->cpt.as<int>() + ld : nullptr;
   d.lu = st->lu.p;
@@ -3015,6 +3018,7 @@ sm_status sm_state_steps(sm_state* st, int32_t m_max, double* d_t, double* d_h, 
 sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* d_cot, int32_t n_cot,
                      double* d_grad, double* d_grad_y0, int32_t* d_astat, int64_t cells_per_pass,
                      void* stream) {
+  if (st && st->d.therm) return SM_ENOTSUP;   // the coupled-temperature adjoint is not built
   if (!st || !d_k || !d_cot || !d_grad || n_cot < 1 || n_cot > SM_ADJ_MAX_COT || st->C < 1 ||
       !ld_ok(st->C, ld) || cells_per_pass < 0 || st->d.record < 1)
     return SM_EINVAL;
@@ -3047,6 +3051,7 @@ sm_status sm_adjoint(sm_state* st, const double* d_k, int64_t ld, const double* 
 
 sm_status sm_replay(sm_state* st, const double* d_k, int64_t ld, double* d_y, int32_t* d_astat,
                     int64_t cells_per_pass, void* stream) {
+  if (st && st->d.therm) return SM_ENOTSUP;
   if (!st || !d_k || !d_y || st->C < 1 || !ld_ok(st->C, ld) || cells_per_pass < 0 || st->d.record < 1)
     return SM_EINVAL;
   if (st->d.mixed) return SM_ENOTSUP;

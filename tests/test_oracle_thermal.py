@@ -170,3 +170,34 @@ def test_temperature_free_rates_reduce_to_fixed_T_chemistry(net):
         err = np.abs(r.y[m][big] - ref.y[m][big]) / ref.y[m][big]
         assert err.max() < 1e-6, (c, err.max())
         assert r.y[th.t_index] != z0[th.t_index, c]   # T itself did evolve
+
+
+def test_solve_step_reproduces_integrator_steps(net):
+    """With a tight Newton tolerance the coupled integrator's accepted steps
+    solve the same equation: solve_step from the recorded history gives every
+    accepted state (T included) to within that tolerance; a history in the
+    wrong order is caught."""
+    d, th = net
+    T, nH, Av, z0 = _cells(d, 1)
+    cell = (nH[0], Av[0], 1.0)
+    t_end = 1e3 * YEAR
+    r = oth.integrate_cell(d, th, cell, z0[:, 0], t_end, ob.BDFOptions(newton_tol=1e-9, newton_max=8),
+                           record=True)
+    assert r.status == ob.STATUS_OK and r.steps > 30
+    acc = [e for e in r.log if e["outcome"] == "accept"]
+    ys, ts = [z0[:, 0]], [0.0]
+    for e in acc:
+        ys.append(e["y"])
+        ts.append(t_end if e["t"] + e["h"] >= t_end else e["t"] + e["h"])
+    for m, e in enumerate(acc):
+        q = e["q"]
+        zm = oth.solve_step(d, th, cell, [ys[m - i] for i in range(q)], [ts[m - i] for i in range(q)],
+                            ts[m + 1], e["h"])
+        w = 1.0 / (1e-6 * np.abs(ys[m]) + 1e-20)
+        assert ob.wrms(zm - ys[m + 1], w) <= 1e-8, m
+    m = next(i for i, e in enumerate(acc) if e["q"] >= 3)
+    q = acc[m]["q"]
+    bad = oth.solve_step(d, th, cell, [ys[m - q + 1 + i] for i in range(q)], [ts[m - i] for i in range(q)],
+                         ts[m + 1], acc[m]["h"])
+    w = 1.0 / (1e-6 * np.abs(ys[m]) + 1e-20)
+    assert ob.wrms(bad - ys[m + 1], w) > 1e-3
