@@ -200,6 +200,33 @@ def _oracle_cell(args):
     return r.steps, time.time() - t0
 
 
+_ORACLE_THERMAL = None
+THERMAL_WORKLOAD = "thermal_470x6000_c16384"
+
+
+def _oracle_thermal_cell(args):
+    """One cell of the coupled-temperature workload integrated by the
+    coupled-temperature oracle: (accepted steps, seconds integrating)."""
+    global _ORACLE_THERMAL
+    c, t_end = args
+    from oracle import network as on
+    from oracle import thermal as oth
+    from synth.workloads import make_thermal
+    if _ORACLE_THERMAL is None or _ORACLE_THERMAL[2].shape[0] <= c:
+        d, th, nH, Av, z0 = make_thermal(THERMAL_WORKLOAD, cells=max(64, c + 1))
+        _ORACLE_THERMAL = (d, th, nH, Av, z0, on.stoichiometry(d))
+    d, th, nH, Av, z0, S = _ORACLE_THERMAL
+    t0 = time.time()
+    r = oth.integrate_cell(d, th, (float(nH[c]), float(Av[c]), 1.0), z0[:, c], t_end, S=S)
+    return r.steps, time.time() - t0
+
+
+def _warm_thermal(_):
+    _oracle_thermal_cell((0, 1e-9))
+    time.sleep(0.5)
+    return 0
+
+
 def _pool_init():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
@@ -230,6 +257,14 @@ class OraclePool:
         """(accepted steps summed, wall seconds) for integrating `cells`."""
         t0 = time.time()
         res = self.pool.map(_oracle_cell, [(c, t_end) for c in cells], chunksize=1)
+        return sum(r[0] for r in res), time.time() - t0
+
+    def run_thermal(self, cells, t_end):
+        """(accepted steps summed, wall seconds) for the coupled-temperature
+        oracle on `cells` of the coupled-temperature workload."""
+        self.pool.map(_warm_thermal, range(2 * self.cores), chunksize=1)
+        t0 = time.time()
+        res = self.pool.map(_oracle_thermal_cell, [(c, t_end) for c in cells], chunksize=1)
         return sum(r[0] for r in res), time.time() - t0
 
     def close(self):
@@ -562,7 +597,7 @@ def pdr_slab(B, dev, precisions=("mixed", "fp64")):
     return out
 
 
-def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
+def thermal_leg(B, dev, cells=4096, precisions=("mixed",), cpu=True):
     """Coupled gas temperature (NEXT row: the energy equation as one more BDF
     component, k'(T) re-evaluated inside every Newton iteration): the first
     `cells` cells of the coupled-temperature workload integrated to 1e6 yr
@@ -571,7 +606,7 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
     import numpy as np
     import torch
     from synth.workloads import WORKLOADS, make_thermal
-    w = WORKLOADS["thermal_470x6000_c16384"]
+    w = WORKLOADS[THERMAL_WORKLOAD]
     d, th, nH, Av, z0 = make_thermal(w.name, cells=cells)
     C = z0.shape[1]
     ld = B.pad_ld(C)
@@ -604,6 +639,18 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
                      "T_final_K": {"min": float(T1.min()), "median": float(np.median(T1)), "max": float(T1.max())}}
         st.close()
     net.close()
+    if cpu:
+        # the oracle on the host cores: the first cells of the same workload,
+        # one single-threaded process per core
+        pool = OraclePool()
+        try:
+            n = min(pool.cores, C)
+            steps, sec = pool.run_thermal(list(range(n)), w.t_end)
+        finally:
+            pool.close()
+        out["oracle_cpu"] = {"cell_steps_per_s": steps / sec, "cells": n, "cores": pool.cores, "seconds": sec,
+                             "sample": f"cells 0-{n - 1} of {w.name}, whole 1e6 yr at rtol 1e-6, "
+                                       "one single-threaded process per core"}
     return out
 
 
@@ -778,7 +825,7 @@ def main():
               "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
               "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
               "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev),
-              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells)}[a.only]
+              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells, cpu=not a.no_cpu)}[a.only]
         if rank == 0:
             print(json.dumps(fn()))
         return
@@ -917,7 +964,7 @@ def main():
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
     pdr = None if a.no_pdr else aux(pdr_slab, B, dev)
-    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells)
+    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells, ("mixed",), not a.no_cpu)
     cpu = None if a.no_cpu else aux(cpu_baseline, t_end)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

@@ -549,8 +549,10 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       acc = warp_sum(acc);
       if (lane == 0) store_m(ds, acc);
     }
-    // the others: a thread each, two entries at a time so that their loads
-    // overlap
+    // the others: a thread each, two entries at a time; the first kJPre term
+    // words of both entries are loaded before any is used, so that their
+    // loads overlap (most entries have at most kJPre terms)
+    constexpr int kJPre = 4;
     for (int p = tid; p < d.nnz_j; p += 2 * nthr) {
       const bool hb = p + nthr < d.nnz_j;
       const int4 da = __ldg(d.jdesc + p);
@@ -558,7 +560,18 @@ __global__ void __launch_bounds__(kRefreshThreads, 2) refresh_kernel(Dev d, cons
       const bool la = da.y - da.x <= kJLong, lb = hb && db.y - db.x <= kJLong;
       double aa = 0.0, ab = 0.0;
       const int na = la ? da.y - da.x : 0, nb = lb ? db.y - db.x : 0;
-      for (int u = 0; u < max(na, nb); ++u) {
+      int2 wa[kJPre], wb[kJPre];
+#pragma unroll
+      for (int u = 0; u < kJPre; ++u) {
+        wa[u] = u < na ? __ldg(d.jt_slot + da.x + u) : make_int2(0, 0);
+        wb[u] = u < nb ? __ldg(d.jt_slot + db.x + u) : make_int2(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < kJPre; ++u) {
+        if (u < na) aa = fma(coef[(uint32_t)wa[u].x >> 24], dR[2 * (wa[u].x & 0xFFFFFF) + wa[u].y], aa);
+        if (u < nb) ab = fma(coef[(uint32_t)wb[u].x >> 24], dR[2 * (wb[u].x & 0xFFFFFF) + wb[u].y], ab);
+      }
+      for (int u = kJPre; u < max(na, nb); ++u) {
         if (u < na) aa = term(aa, da.x + u);
         if (u < nb) ab = term(ab, db.x + u);
       }
