@@ -602,7 +602,8 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",), cpu=True):
     component, k'(T) re-evaluated inside every Newton iteration): the first
     `cells` cells of the coupled-temperature workload integrated to 1e6 yr
     as one whole simulation timed with CUDA events (sm_state_set_cells +
-    sm_integrate, after an untimed run that captures the graphs)."""
+    sm_integrate, after an untimed run that captures the graphs), beside the
+    same cells at fixed T and the coupled-temperature oracle on the host."""
     import numpy as np
     import torch
     from synth.workloads import WORKLOADS, make_thermal
@@ -639,6 +640,32 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",), cpu=True):
                      "T_final_K": {"min": float(T1.min()), "median": float(np.median(T1)), "max": float(T1.max())}}
         st.close()
     net.close()
+    # the same cells with T held at its initial value (the paper's fixed-T
+    # chemistry step): the chemical network alone, k' from each cell's T
+    from synth.workloads import make
+    d0, T0, _, _, y0 = make(w.name, cells=cells)
+    net0 = B.Network(d0, dev.index or 0)
+    Td, nHd0, Avd0 = device_conditions(B, T0, nH, Av, dev)
+    kd = torch.empty((d0.n_r, ld), dtype=torch.float64, device=dev)
+    y0d = torch.zeros((d0.n_s, ld), dtype=torch.float64, device=dev)
+    y0d[:, :C] = vec(y0)
+    st = B.State(net0, C, precision=precisions[0])
+    stats = B.stats_tensor(C, dev)
+    yd = y0d.clone()
+
+    def run0():
+        net0.rates_eval(Td, nHd0, Avd0, kd, C)
+        yd.copy_(y0d)
+        return st.integrate(kd, yd, w.t_end, C, stats)
+
+    run0()
+    code, ms = timed(run0, stream)
+    s = B.stats_to_numpy(stats)
+    out["fixed_T_" + precisions[0]] = {"seconds": ms * 1e-3,
+                                       "cell_steps_per_s": float(s["steps"].sum()) / (ms * 1e-3),
+                                       "steps_per_cell": float(s["steps"].mean()), "status": int(code)}
+    st.close()
+    net0.close()
     if cpu:
         # the oracle on the host cores: the first cells of the same workload,
         # one single-threaded process per core
