@@ -26,8 +26,13 @@ After the headline line's own measurements the same JSON line carries:
                   4096 cells, against the FP64-pipe ceiling
   pdr_slab        the paper's PDR benchmark geometry (128 cells, 30 Myr) as
                   one whole simulation, mixed and FP64
+  thermal         coupled gas temperature: 4096 cells of the coupled-
+                  temperature workload to 1e6 yr, beside the same cells at
+                  fixed T
+  single_cell     the 32 x 180 network, one cell to 1e6 yr (config 0)
   cpu_baseline    the oracle on the host cores: 64 stratified cells, each
-                  integrated over the whole interval
+                  integrated over the whole interval; beside it the
+                  coupled-temperature oracle on 16 cells and the single cell
 
     python bench.py [--gpus N --steps K --warmup W] [--precision mixed|tf32|fp64]
     python bench.py --impl reference ...      # the CPU oracle on a sample
@@ -105,7 +110,8 @@ def args_():
                    help="cells of the rhs_eval / jac_eval format grid (0 = skip)")
     p.add_argument("--budget-s", type=float, default=1200.0,
                    help="auxiliary measurements start only while the run is younger than this")
-    p.add_argument("--only", default="", choices=["", "rhs", "mixed", "adjoint", "cpu", "probe", "pdr", "thermal"],
+    p.add_argument("--only", default="",
+                   choices=["", "rhs", "mixed", "adjoint", "cpu", "probe", "pdr", "thermal", "single"],
                    help="run one auxiliary measurement alone and print it")
     p.add_argument("--phases", action="store_true",
                    help="refresh-kernel cycles per phase over one integration (phase-clock build)")
@@ -227,6 +233,20 @@ def _warm_thermal(_):
     return 0
 
 
+def _oracle_single_cell():
+    """Config 0 on the oracle: the 32 x 180 network, one cell, 1e6 yr, one
+    core (seconds and accepted steps)."""
+    from oracle import bdf as ob
+    from oracle import kinetics as ok
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["single_cell_32x180"]
+    d, T, nH, Av, y0 = make(w.name)
+    t0 = time.time()
+    k = ok.rate_coefficients(d, T, nH, Av)
+    r = ob.integrate_cell(d, k[:, 0], y0[:, 0], w.t_end)
+    return {"workload": w.name, "seconds": time.time() - t0, "steps": int(r.steps)}
+
+
 def _pool_init():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
@@ -272,15 +292,28 @@ class OraclePool:
         self.pool.join()
 
 
-def cpu_baseline(t_end):
+def cpu_baseline(t_end, thermal_cells=0):
+    """The oracle on the host cores: the headline workload's stratified
+    sample (the line's cpu_baseline), and beside it the coupled-temperature
+    oracle on the first cells of that workload (thermal_cells > 0) and the
+    single-cell 32 x 180 case (config 0) on one core."""
     cells, _ = stratified_cells()
     pool = OraclePool()
+    extra = {}
     try:
         pool.warm()                                 # process start-up and imports, untimed
         steps, dt = pool.run(cells, t_end)
+        if thermal_cells > 0:
+            from synth.workloads import WORKLOADS
+            n = min(pool.cores, thermal_cells)
+            tsteps, tsec = pool.run_thermal(list(range(n)), WORKLOADS[THERMAL_WORKLOAD].t_end)
+            extra["thermal"] = {"value": tsteps / tsec, "unit": UNIT, "cells": n, "seconds": tsec,
+                                "sample": f"cells 0-{n - 1} of {THERMAL_WORKLOAD}, whole 1e6 yr at rtol 1e-6, "
+                                          "one single-threaded process per core"}
     finally:
         pool.close()
-    return {"value": steps / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+    extra["single_cell"] = _oracle_single_cell()
+    return {"value": steps / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle", **extra,
             "sample": (f"{len(cells)} cells of {WORKLOAD} stratified by stiffness (evenly spaced quantiles of "
                        f"the oracle's step count among every 128th of the first 16,384 cells), each integrated "
                        f"over the whole 1e6 yr at rtol 1e-6, one single-threaded process per core; "
@@ -597,13 +630,46 @@ def pdr_slab(B, dev, precisions=("mixed", "fp64")):
     return out
 
 
-def thermal_leg(B, dev, cells=4096, precisions=("mixed",), cpu=True):
+def single_cell(B, dev):
+    """Config 0: the 32 x 180 network, one cell (T 10 K, n_H 1e4, A_V 5,
+    atomic start) to 1e6 yr at rtol 1e-6: GPU wall time of sm_rates_eval +
+    sm_integrate (FP64, after an untimed run that captures the graphs); the
+    oracle's time for the same cell is in cpu_baseline["single_cell"]."""
+    import torch
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["single_cell_32x180"]
+    d, T, nH, Av, y0 = make(w.name)
+    ld = B.pad_ld(1)
+    net = B.Network(d, dev.index or 0)
+    Td, nHd, Avd = device_conditions(B, T, nH, Av, dev)
+    kd = torch.empty((d.n_r, ld), dtype=torch.float64, device=dev)
+    y0d = torch.zeros((d.n_s, ld), dtype=torch.float64, device=dev)
+    y0d[:, :1] = torch.tensor(y0, dtype=torch.float64, device=dev)
+    st = B.State(net, 1)
+    stats = B.stats_tensor(1, dev)
+    yd = y0d.clone()
+
+    def run():
+        net.rates_eval(Td, nHd, Avd, kd, 1)
+        yd.copy_(y0d)
+        return st.integrate(kd, yd, w.t_end, 1, stats)
+
+    run()
+    code, ms = timed(run, torch.cuda.current_stream(dev))
+    s = B.stats_to_numpy(stats)
+    st.close()
+    net.close()
+    return {"workload": w.name, "gpu_ms": ms, "steps": int(s["steps"][0]), "status": int(code)}
+
+
+def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
     """Coupled gas temperature (NEXT row: the energy equation as one more BDF
     component, k'(T) re-evaluated inside every Newton iteration): the first
     `cells` cells of the coupled-temperature workload integrated to 1e6 yr
     as one whole simulation timed with CUDA events (sm_state_set_cells +
     sm_integrate, after an untimed run that captures the graphs), beside the
-    same cells at fixed T and the coupled-temperature oracle on the host."""
+    same cells at fixed T (the coupled-temperature oracle's time is in
+    cpu_baseline["thermal"])."""
     import numpy as np
     import torch
     from synth.workloads import WORKLOADS, make_thermal
@@ -666,18 +732,6 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",), cpu=True):
                                        "steps_per_cell": float(s["steps"].mean()), "status": int(code)}
     st.close()
     net0.close()
-    if cpu:
-        # the oracle on the host cores: the first cells of the same workload,
-        # one single-threaded process per core
-        pool = OraclePool()
-        try:
-            n = min(pool.cores, C)
-            steps, sec = pool.run_thermal(list(range(n)), w.t_end)
-        finally:
-            pool.close()
-        out["oracle_cpu"] = {"cell_steps_per_s": steps / sec, "cells": n, "cores": pool.cores, "seconds": sec,
-                             "sample": f"cells 0-{n - 1} of {w.name}, whole 1e6 yr at rtol 1e-6, "
-                                       "one single-threaded process per core"}
     return out
 
 
@@ -829,7 +883,7 @@ def main():
     if a.impl == "reference":
         return reference_arm(a, rank)
     if a.only == "cpu":
-        print(json.dumps(cpu_baseline(a.t_end_yr * YEAR)))
+        print(json.dumps(cpu_baseline(a.t_end_yr * YEAR, max(a.thermal_cells, 0))))
         return
     import numpy as np
     import torch
@@ -852,7 +906,8 @@ def main():
               "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
               "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
               "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev),
-              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells, cpu=not a.no_cpu)}[a.only]
+              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells),
+              "single": lambda: single_cell(B, dev)}[a.only]
         if rank == 0:
             print(json.dumps(fn()))
         return
@@ -991,8 +1046,9 @@ def main():
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
     pdr = None if a.no_pdr else aux(pdr_slab, B, dev)
-    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells, ("mixed",), not a.no_cpu)
-    cpu = None if a.no_cpu else aux(cpu_baseline, t_end)
+    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells)
+    single = aux(single_cell, B, dev)
+    cpu = None if a.no_cpu else aux(cpu_baseline, t_end, max(a.thermal_cells, 0))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -1009,10 +1065,14 @@ def main():
                   "newton_per_cell": float(s["newton_iters"].mean()),
                   "jac_per_cell": float(s["jac_evals"].mean()),
                   "rejects_per_cell": float(s["rejects"].mean()),
-                  "cells_ok": int((s["status"] == 0).sum())},
+                  "cells_ok": int((s["status"] == 0).sum()),
+                  # per-cell distributions (config 2 asks for the histograms):
+                  # deciles 0, 10, ..., 100 % over the cells
+                  "deciles": {key: np.percentile(s[key], np.arange(0, 101, 10)).round(1).tolist()
+                              for key in ("steps", "rejects", "newton_iters", "jac_evals")}},
         "gpu_launches": int(launches),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "pdr_slab": pdr, "thermal": therm, "peaks": peaks,
+        "fp64_vs_mixed": mixed, "adjoint": adj, "rhs_jac": rhs, "pdr_slab": pdr, "thermal": therm, "single_cell": single, "peaks": peaks,
         "wall_s": time.time() - t_start,
     }
     print(json.dumps(out))
