@@ -606,3 +606,50 @@ def test_integrator_gather_shapes(torch, B, moderate_case, order, kc):
     assert cell_err(out[1], out[0]).max() <= 50.0
     yo = np.stack([r.y for r in ref], axis=1)
     assert cell_err(out[1], yo).max() <= 100.0
+
+
+def test_full_size_batch_matches_oracle_on_sampled_cells(torch, B, strat_case):
+    """The benchmark's launch configuration: all 65,536 cells of the headline
+    workload (470 x 6000, T 10-1000 K, n_H 1e2-1e8, A_V 0-20, atomic start,
+    1e6 yr) integrated as one batch in the mixed mode with the autotuned
+    gather, graphs and compaction, as bench.py times it.  The 32 stratified
+    cells of the stored truth are the same draws (cells are a seeded stream,
+    so the first 16,384 of the batch are the truth's pool); they take the
+    mixed-precision bars of test_large_network_matches_oracle, and every
+    cell of the batch must finish."""
+    from synth.workloads import make
+    d, k_small, y0_small, t_end, truth, yo, steps_o = strat_case
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "integrate_truth_strat.json")) as fh:
+        cells = json.load(fh)["cells"]
+    dd, T, nH, Av, y0 = make("integrate_470x6000_c65536")
+    C = y0.shape[1]
+    assert np.array_equal(y0[:, cells], y0_small)
+    ld = B.pad_ld(C)
+    net = B.Network(dd, 0)
+    vec = lambda a, fill: torch.cat([torch.tensor(a, dtype=torch.float64),
+                                     torch.full((ld - C,), fill, dtype=torch.float64)]).cuda()
+    Td, nHd, Avd = vec(T, 100.0), vec(nH, 1.0), vec(Av, 0.0)
+    kd = torch.empty((dd.n_r, ld), dtype=torch.float64, device="cuda")
+    net.rates_eval(Td, nHd, Avd, kd, C)
+    assert np.allclose(kd[:, cells].cpu().numpy(), k_small, rtol=1e-13, atol=0.0)
+    yd = torch.zeros((dd.n_s, ld), dtype=torch.float64, device="cuda")
+    yd[:, :C] = torch.tensor(y0, dtype=torch.float64, device="cuda")
+    fscr = torch.empty_like(yd)
+    net.autotune(kd, yd, fscr, C)
+    del fscr
+    st = B.State(net, C, precision="mixed")
+    stats = B.stats_tensor(C, "cuda")
+    code = st.integrate(kd, yd, t_end, C, stats)
+    torch.cuda.synchronize()
+    s = B.stats_to_numpy(stats)
+    assert code == B.SM_OK and np.all(s["status"] == B.CELL_OK)
+    y = yd[:, cells].cpu().numpy()
+    e_o = np.maximum(cell_err(yo, truth), 1.0)
+    e_g = np.maximum(cell_err(y, truth), 1.0)
+    assert e_g.max() <= 100.0, (e_g.max(), int(e_g.argmax()))
+    assert e_g.max() <= 2.0 * e_o.max(), (e_g.max(), e_o.max())
+    assert np.median(e_g) <= 1.5 * np.median(e_o), (np.median(e_g), np.median(e_o))
+    st_s = s["steps"][cells]
+    assert np.all(np.abs(st_s - steps_o) <= 0.25 * steps_o + 10)

@@ -76,6 +76,26 @@ def cell_err(y, ref, rtol=1e-6, atol=1e-20):
     return np.max(np.abs(y - ref) / (rtol * np.abs(ref) + atol), axis=0)
 
 
+def check_element_drift(d, th, z0, z, z_o, stats, precision):
+    """Element totals (H, C, O) of the chemical rows: the coupled Newton
+    correction keeps E y fixed like the fixed-T one (E S = 0 gives E u = 0
+    and E z = 0 for the temperature border), so the drift bars of the
+    fixed-T tests apply: FP64 within FP64_DRIFT_FACTOR of the oracle's
+    largest drift (its rtol-1e-6 run, z_o), reduced precisions within
+    fp32_drift_bar."""
+    from oracle.network import element_matrix
+    from tests.test_gpu_integrate import FP64_DRIFT_FACTOR, fp32_drift_bar
+    E = element_matrix(d).astype(float)[:3]
+    tot0 = np.abs(E @ z0)
+    drift = (np.abs(E @ z - E @ z0) / tot0).max(axis=0)
+    drift_o = (np.abs(E @ z_o - E @ z0) / tot0).max(axis=0)
+    if precision == "fp64":
+        assert drift.max() <= FP64_DRIFT_FACTOR * max(drift_o.max(), 1e-13), (drift.max(), drift_o.max())
+    else:
+        bar = fp32_drift_bar(stats, drift_o.max())
+        assert np.all(drift <= bar), (drift / bar).max()
+
+
 def _frozen(d):
     """Rate coefficients so small that the chemistry is frozen (the library
     requires alpha > 0): every reaction rate below 1e-250."""
@@ -200,6 +220,7 @@ def test_small_network_matches_oracle(torch, B, precision):
     # the temperature itself: within 1e-4 relative of the truth everywhere
     t = th.t_index
     assert np.all(np.abs(z[t] - y10[t]) <= 1e-4 * y10[t]), np.abs(z[t] / y10[t] - 1).max()
+    check_element_drift(d, th, z0, z, y6, stats, precision)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -220,6 +241,7 @@ def test_large_network_matches_oracle(torch, B, precision):
     assert np.all(np.abs(stats["steps"] - steps_o) <= 0.25 * steps_o + 10), (stats["steps"], steps_o)
     t = th.t_index
     assert np.all(np.abs(z[t] - y10[t]) <= 1e-4 * y10[t]), np.abs(z[t] / y10[t] - 1).max()
+    check_element_drift(d, th, z0, z, y6, stats, precision)
 
 
 def test_fixed_temperature_limit_matches_plain_integrator(torch, B):
@@ -317,3 +339,26 @@ def test_step_replay_matches_oracle(torch, B, precision):
     errs = np.array(errs)
     assert len(errs) > 100
     assert errs.max() <= 1.0, (errs.max(), np.quantile(errs, 0.99))
+
+
+def test_bench_batch_matches_oracle_on_sampled_cells(torch, B):
+    """The thermal bench leg's launch configuration: the first 4096 cells of
+    the coupled-temperature workload as one batch (mixed precision); the 8
+    cells of the stored large-network truth are among them (cells are a
+    seeded stream) and take the bars of test_large_network_matches_oracle."""
+    from synth.workloads import make_thermal
+    ref = truth("thermal_large")
+    cells = ref["cells"]
+    d, th, nH, Av, z0 = make_thermal("thermal_470x6000_c16384", cells=4096)
+    from tests.golden.make_integrate_truth import thermal_inputs
+    _, _, nH_s, Av_s, z0_s = thermal_inputs(470, 6000, cells)
+    assert np.array_equal(nH[cells], nH_s) and np.array_equal(z0[:, cells], z0_s)
+    z, stats, code = run_thermal(torch, B, d, th, nH, Av, z0, ref["t_end"], precision="mixed")
+    assert code == B.SM_OK and np.all(stats["status"] == B.CELL_OK)
+    y10, y6 = np.array(ref["y"]).T, np.array(ref["y_rtol6"]).T
+    zs = z[:, cells]
+    e_g, e_o = np.maximum(cell_err(zs, y10), 1.0), np.maximum(cell_err(y6, y10), 1.0)
+    assert e_g.max() <= 100.0 and e_g.max() <= 3.0 * e_o.max(), (e_g.max(), e_o.max())
+    assert np.median(e_g) <= 2.0 * np.median(e_o), (np.median(e_g), np.median(e_o))
+    t = th.t_index
+    assert np.all(np.abs(zs[t] - y10[t]) <= 1e-4 * y10[t]), np.abs(zs[t] / y10[t] - 1).max()
