@@ -231,59 +231,78 @@ __global__ void init_finish_kernel(Dev d) {
 // ---------------------------------------------------------------------------
 // predict
 // ---------------------------------------------------------------------------
-__global__ void predict_kernel(Dev d) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C || (d.compact && c >= d.counters[kCAct])) return;
-  int fl = d.flags[c] & ~(F_CONV | F_FAILED | F_REFRESH | F_FINAL | F_NEWTON | F_ATTEMPT);
-  if (d.status[c] != SM_CELL_RUNNING) {
-    d.flags[c] = fl;
-    return;
-  }
-  atomicAdd(&d.counters[1], 1);
-  if (d.steps[c] >= d.max_steps) {
-    d.status[c] = SM_CELL_MAXSTEPS;
-    d.flags[c] = fl;
-    return;
-  }
-  const double t = d.t[c];
-  double h = d.h[c];
-  const int q = d.q[c], nh = d.nh[c];
-  const bool fin = t + h >= d.t_end;
-  if (fin) h = d.t_end - t;
-  const double tnew = fin ? d.t_end : t + h;
-  if (tnew == t || !(h > 0.0)) {
-    d.status[c] = SM_CELL_HMIN;
-    d.flags[c] = fl;
-    return;
-  }
+// Predict and finish work on 32 cells per CTA with kCoopWarps warps: every
+// warp derives a cell's step scalars from the same inputs (identical
+// results), warp 0 alone writes them back, and the species loops are split
+// over the warps (lane = cell, so every row access is a coalesced 256-byte
+// line).  A thread per cell over all species left too few warps to hide
+// the memory latency when few cells run.
+constexpr int kCoopWarps = 8;
+
+__global__ void __launch_bounds__(32 * kCoopWarps) predict_kernel(Dev d) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = c < d.C && !(d.compact && c >= d.counters[kCAct]);
+  int fl = 0, q = 1, nh = 1, state = 0;   // state: 0 idle, 1 max steps, 2 step too small, 3 attempt
+  double h = 0.0, gamma = 0.0;
+  bool fin = false, refresh = false;
   double T[QMAX + 1], wts[QMAX + 1], al[QMAX + 1];
-  for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
-  if (nh > 1) lagrange(T, q + 1, tnew, wts);
-  bdf_alphas(tnew, T, q, h, al);
-  const double gamma = h / al[0];
-  const bool refresh = (fl & F_NEED_J) || d.j_age[c] >= d.j_age_max ||
-                       fabs(gamma / d.gam_J[c] - 1.0) > d.gamma_tol;
-  d.h[c] = h;
-  d.gam[c] = gamma;
-  for (int i = 0; i <= q; ++i) d.alpha[(int64_t)i * d.ld + c] = al[i];
-  d.flags[c] = fl | F_NEWTON | F_ATTEMPT | (fin ? F_FINAL : 0) | (refresh ? F_REFRESH : 0);
-  d.m_it[c] = 0;
-  d.dprev[c] = 0.0;
-  if (refresh) d.list[atomicAdd(&d.counters[0], 1)] = (int)c;
+  if (live) {
+    fl = d.flags[c] & ~(F_CONV | F_FAILED | F_REFRESH | F_FINAL | F_NEWTON | F_ATTEMPT);
+    if (d.status[c] == SM_CELL_RUNNING) {
+      if (d.steps[c] >= d.max_steps) {
+        state = 1;
+      } else {
+        const double t = d.t[c];
+        h = d.h[c];
+        q = d.q[c];
+        nh = d.nh[c];
+        fin = t + h >= d.t_end;
+        if (fin) h = d.t_end - t;
+        const double tnew = fin ? d.t_end : t + h;
+        if (tnew == t || !(h > 0.0)) {
+          state = 2;
+        } else {
+          state = 3;
+          for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
+          if (nh > 1) lagrange(T, q + 1, tnew, wts);
+          bdf_alphas(tnew, T, q, h, al);
+          gamma = h / al[0];
+          refresh = (fl & F_NEED_J) || d.j_age[c] >= d.j_age_max || fabs(gamma / d.gam_J[c] - 1.0) > d.gamma_tol;
+        }
+      }
+    }
+  }
+  __syncthreads();   // every warp has read the cell before warp 0 rewrites it
+  if (wi == 0 && live) {
+    if (d.status[c] == SM_CELL_RUNNING) atomicAdd(&d.counters[1], 1);
+    if (state == 1) d.status[c] = SM_CELL_MAXSTEPS;
+    if (state == 2) d.status[c] = SM_CELL_HMIN;
+    if (state == 3) {
+      d.h[c] = h;
+      d.gam[c] = gamma;
+      for (int i = 0; i <= q; ++i) d.alpha[(int64_t)i * d.ld + c] = al[i];
+      fl |= F_NEWTON | F_ATTEMPT | (fin ? F_FINAL : 0) | (refresh ? F_REFRESH : 0);
+      d.m_it[c] = 0;
+      d.dprev[c] = 0.0;
+      if (refresh) d.list[atomicAdd(&d.counters[0], 1)] = (int)c;
+    }
+    d.flags[c] = fl;
+  }
+  if (state != 3) return;
   // kPU species at a time with the history loops unrolled, so that each
-  // thread has kPU * (q + 1) loads in flight (one thread per cell leaves too
-  // few warps to cover the memory latency otherwise)
+  // thread has kPU * (q + 1) loads in flight
   constexpr int kPU = 4;
   const bool euler = nh == 1;
-  for (int s0 = 0; s0 < d.n; s0 += kPU) {
+  for (int s0 = wi * kPU; s0 < d.n; s0 += kCoopWarps * kPU) {
     double Yv[kPU][QMAX + 1], fv[kPU];
 #pragma unroll
     for (int u = 0; u < kPU; ++u) {
       const int64_t o = (int64_t)(s0 + u) * d.ld + c;
-      const bool live = s0 + u < d.n;
+      const bool in = s0 + u < d.n;
 #pragma unroll
-      for (int i = 0; i <= QMAX; ++i) Yv[u][i] = (live && i <= q && i < nh) ? Yh(d, i)[o] : 0.0;
-      fv[u] = (live && euler) ? d.f0[o] : 0.0;
+      for (int i = 0; i <= QMAX; ++i) Yv[u][i] = (in && i <= q && i < nh) ? Yh(d, i)[o] : 0.0;
+      fv[u] = (in && euler) ? d.f0[o] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kPU; ++u) {
@@ -1464,15 +1483,120 @@ __global__ void __launch_bounds__(32 * kBorderWarps) th_border_kernel(Dev d) {
 // ---------------------------------------------------------------------------
 // finish: error test, step / order selection, history update
 // ---------------------------------------------------------------------------
-__global__ void finish_kernel(Dev d) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d.C || (d.compact && c >= d.counters[kCAct])) return;
-  int fl = d.flags[c];
-  if (!(fl & F_ATTEMPT)) return;
-  fl &= ~F_ATTEMPT;
+__global__ void __launch_bounds__(32 * kCoopWarps) finish_kernel(Dev d) {
+  // partial WRMS sums of the warps (error test, then the two neighbouring orders)
+  __shared__ double red_e[kCoopWarps][32], red_lo[kCoopWarps][32], red_hi[kCoopWarps][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = c < d.C && !(d.compact && c >= d.counters[kCAct]);
   const int n = d.n;
-  const int q = d.q[c], nh = d.nh[c];
-  double h = d.h[c];
+  int fl = live ? d.flags[c] : 0;
+  const bool go = (fl & F_ATTEMPT) != 0;
+  fl &= ~F_ATTEMPT;
+  const bool work = go && !(fl & F_FAILED);   // an error test to run
+  int q = 1, nh = 1;
+  double h = 0.0, tnew = 0.0;
+  double T[QMAX + 1];
+  if (go) {
+    q = d.q[c];
+    nh = d.nh[c];
+    h = d.h[c];
+  }
+  if (work) {
+    tnew = (fl & F_FINAL) ? d.t_end : d.t[c] + h;
+    for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
+  }
+  // pass 1: the error estimate, species split over the warps
+  double acc = 0.0;
+  if (work) {
+#pragma unroll 4
+    for (int s = wi; s < n; s += kCoopWarps) {
+      const int64_t o = (int64_t)s * d.ld + c;
+      const double v = (d.y[o] - d.ypred[o]) * d.w[o];
+      acc += v * v;
+    }
+  }
+  red_e[wi][lane] = acc;
+  __syncthreads();
+  acc = 0.0;
+  for (int w = 0; w < kCoopWarps; ++w) acc += red_e[w][lane];   // same order in every warp
+  const double err = work ? (nh >= q + 1 ? h / (tnew - T[q]) : 1.0 / (q + 1)) * sqrt(acc / n) : 0.0;
+  const bool accepted = work && isfinite(err) && err <= 1.0;
+  // pass 2: rate the neighbouring orders on the old history
+  const int naq = accepted ? d.n_at_q[c] + 1 : 0;
+  const bool lo = accepted && naq >= q + 1 && q > 1;
+  const bool hi = accepted && naq >= q + 1 && q < d.q_max && (fl & F_HAS_EPREV) && nh + 1 >= q + 2;
+  double wl[QMAX + 1];
+  if (lo) lagrange(T, q, tnew, wl);
+  double acc_lo = 0.0, acc_hi = 0.0;
+  if (lo || hi) {
+#pragma unroll 2
+    for (int s = wi; s < n; s += kCoopWarps) {
+      const int64_t o = (int64_t)s * d.ld + c;
+      const double yv = d.y[o], wv = d.w[o];
+      if (lo) {
+        double p = 0.0;
+#pragma unroll
+        for (int i = 0; i < QMAX; ++i)
+          if (i < q) p += wl[i] * Yh(d, i)[o];
+        const double v = (yv - p) * wv;
+        acc_lo += v * v;
+      }
+      if (hi) {
+        const double v = ((yv - d.ypred[o]) - d.eprev[o]) * wv;
+        acc_hi += v * v;
+      }
+    }
+  }
+  red_lo[wi][lane] = acc_lo;
+  red_hi[wi][lane] = acc_hi;
+  __syncthreads();
+  acc_lo = acc_hi = 0.0;
+  for (int w = 0; w < kCoopWarps; ++w) {
+    acc_lo += red_lo[w][lane];
+    acc_hi += red_hi[w][lane];
+  }
+  double best_eta = accepted ? 0.9 * pow(fmax(err, 1e-10), -1.0 / (q + 1)) : 0.0;
+  int best_q = q;
+  if (lo) {
+    const double est = h / (tnew - T[q - 1]) * sqrt(acc_lo / n);
+    const double eta_lo = 0.8 * pow(fmax(est, 1e-10), -1.0 / q);
+    if (eta_lo > best_eta) {
+      best_eta = eta_lo;
+      best_q = q - 1;
+    }
+  }
+  if (hi) {
+    const double est = sqrt(acc_hi / n) / (q + 2);
+    const double eta_hi = 0.7 * pow(fmax(est, 1e-10), -1.0 / (q + 2));
+    if (eta_hi > best_eta) {
+      best_eta = eta_hi;
+      best_q = q + 1;
+    }
+  }
+  // pass 3: shift the history of the accepted cells, newest first (each warp
+  // its own species, which pass 2 read before)
+  const int nh_new = min(nh + 1, d.q_max + 1);
+  const bool keep_e = best_q == q;
+  if (accepted) {
+#pragma unroll 4
+    for (int s = wi; s < n; s += kCoopWarps) {
+      const int64_t o = (int64_t)s * d.ld + c;
+      double Yv[QMAX];
+#pragma unroll
+      for (int i = 0; i < QMAX; ++i) Yv[i] = i < nh_new - 1 ? Yh(d, i)[o] : 0.0;
+      const double yv = d.y[o];
+      const double yp = keep_e ? d.ypred[o] : 0.0;
+#pragma unroll
+      for (int i = 0; i < QMAX; ++i)
+        if (i < nh_new - 1) Yh(d, i + 1)[o] = Yv[i];
+      if (keep_e) d.eprev[o] = yv - yp;
+      Yh(d, 0)[o] = yv;
+    }
+  }
+  __syncthreads();   // the history is complete (checkpoints read it)
+  if (wi != 0 || !go) return;
+  // the cell's scalars, warp 0 alone
   if (fl & F_FAILED) {
     d.conv_fails[c] += 1;
     const int cf = d.ccf[c] + 1;
@@ -1487,19 +1611,6 @@ __global__ void finish_kernel(Dev d) {
     d.flags[c] = fl;
     return;
   }
-  const double t = d.t[c];
-  const double tnew = (fl & F_FINAL) ? d.t_end : t + h;
-  double T[QMAX + 1];
-  for (int i = 0; i < nh; ++i) T[i] = d.tn[(int64_t)i * d.ld + c];
-  double acc = 0.0;
-#pragma unroll 8
-  for (int s = 0; s < n; ++s) {
-    const int64_t o = (int64_t)s * d.ld + c;
-    const double v = (d.y[o] - d.ypred[o]) * d.w[o];
-    acc += v * v;
-  }
-  const double Cq = nh >= q + 1 ? h / (tnew - T[q]) : 1.0 / (q + 1);
-  const double err = Cq * sqrt(acc / n);
   if (!isfinite(err)) {
     d.status[c] = SM_CELL_NAN;
     d.flags[c] = fl;
@@ -1518,69 +1629,6 @@ __global__ void finish_kernel(Dev d) {
     d.h[c] = h * eta;
     d.flags[c] = fl | F_REJECTED;
     return;
-  }
-  // accepted: rate neighbouring orders on the old history
-  const int naq = d.n_at_q[c] + 1;
-  double best_eta = 0.9 * pow(fmax(err, 1e-10), -1.0 / (q + 1));
-  int best_q = q;
-  if (naq >= q + 1) {
-    const bool lo = q > 1;
-    const bool hi = q < d.q_max && (fl & F_HAS_EPREV) && nh + 1 >= q + 2;
-    if (lo || hi) {
-      double wl[QMAX + 1];
-      if (lo) lagrange(T, q, tnew, wl);
-      double acc_lo = 0.0, acc_hi = 0.0;
-#pragma unroll 4
-      for (int s = 0; s < n; ++s) {
-        const int64_t o = (int64_t)s * d.ld + c;
-        const double yv = d.y[o], wv = d.w[o];
-        if (lo) {
-          double p = 0.0;
-#pragma unroll
-          for (int i = 0; i < QMAX; ++i)
-            if (i < q) p += wl[i] * Yh(d, i)[o];
-          const double v = (yv - p) * wv;
-          acc_lo += v * v;
-        }
-        if (hi) {
-          const double v = ((yv - d.ypred[o]) - d.eprev[o]) * wv;
-          acc_hi += v * v;
-        }
-      }
-      if (lo) {
-        const double est = h / (tnew - T[q - 1]) * sqrt(acc_lo / n);
-        const double eta_lo = 0.8 * pow(fmax(est, 1e-10), -1.0 / q);
-        if (eta_lo > best_eta) {
-          best_eta = eta_lo;
-          best_q = q - 1;
-        }
-      }
-      if (hi) {
-        const double est = sqrt(acc_hi / n) / (q + 2);
-        const double eta_hi = 0.7 * pow(fmax(est, 1e-10), -1.0 / (q + 2));
-        if (eta_hi > best_eta) {
-          best_eta = eta_hi;
-          best_q = q + 1;
-        }
-      }
-    }
-  }
-  // commit: shift the history, newest first
-  const int nh_new = min(nh + 1, d.q_max + 1);
-  const bool keep_e = best_q == q;
-#pragma unroll 4
-  for (int s = 0; s < n; ++s) {
-    const int64_t o = (int64_t)s * d.ld + c;
-    double Yv[QMAX];
-#pragma unroll
-    for (int i = 0; i < QMAX; ++i) Yv[i] = i < nh_new - 1 ? Yh(d, i)[o] : 0.0;
-    const double yv = d.y[o];
-    const double yp = keep_e ? d.ypred[o] : 0.0;
-#pragma unroll
-    for (int i = 0; i < QMAX; ++i)
-      if (i < nh_new - 1) Yh(d, i + 1)[o] = Yv[i];
-    if (keep_e) d.eprev[o] = yv - yp;
-    Yh(d, 0)[o] = yv;
   }
   for (int i = nh_new - 1; i >= 1; --i) d.tn[(int64_t)i * d.ld + c] = T[i - 1];
   d.tn[c] = tnew;
@@ -2238,7 +2286,7 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
   sm_status r;
   SM_TRY_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(int), s));
   if ((r = time_mark(st, SM_TIME_PREDICT, true, s)) != SM_OK) return r;
-  predict_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
+  predict_kernel<<<blocks(d.C, 32), 32 * kCoopWarps, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_PREDICT, false, s)) != SM_OK) return r;
   if ((r = time_mark(st, SM_TIME_REFRESH, true, s)) != SM_OK) return r;
   if (d.kslot) {
@@ -2299,7 +2347,7 @@ sm_status enqueue_attempt(sm_state* st, const double* k, int64_t ldk, cudaStream
     SM_TRY_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
   }
   if ((r = time_mark(st, SM_TIME_FINISH, true, s)) != SM_OK) return r;
-  finish_kernel<<<blocks(d.C, 128), 128, 0, s>>>(d);
+  finish_kernel<<<blocks(d.C, 32), 32 * kCoopWarps, 0, s>>>(d);
   if ((r = time_mark(st, SM_TIME_FINISH, false, s)) != SM_OK) return r;
   SM_TRY_CUDA(cudaGetLastError());
   st->launches += kLaunchesFixed + 3 * d.newton_max * (split ? 2 : 1);
