@@ -79,7 +79,7 @@ PEAK_FP64 = SM_COUNT * 4 * SM_GHZ / 1e3           # TFLOP/s
 TRAFFIC = {
     # profiles/refresh_kernel_mixed_2048cells.md: 11.47 GB in a launch that
     # refreshed all 2048 cells
-    ("refresh", "mixed", "0c783d6fa1d05e59"): 5.603e6,
+    ("refresh", "mixed", "2d7363fd734965ce"): 5.599e6,
 }
 
 
