@@ -653,3 +653,50 @@ def test_full_size_batch_matches_oracle_on_sampled_cells(torch, B, strat_case):
     assert np.median(e_g) <= 1.5 * np.median(e_o), (np.median(e_g), np.median(e_o))
     st_s = s["steps"][cells]
     assert np.all(np.abs(st_s - steps_o) <= 0.25 * steps_o + 10)
+
+
+def test_integrate_rejects_bad_calls(torch, B):
+    """Argument checks of the integrator's entry points (all on the host,
+    before any launch): empty or oversized batches, a row stride that is not
+    a multiple of 32, missing rate coefficients, a non-positive end time,
+    out-of-range options; each returns SM_EINVAL and leaves the state usable."""
+    import ctypes as ct
+    d = sn.generate(2312, 32, 180)
+    C = 8
+    ld = B.pad_ld(C)
+    net = B.Network(d, 0)
+    st = B.State(net, C)
+    T, nH, Av = sc.conditions(4998, C, (10.0, 300.0), (1e2, 1e6), (0.0, 10.0))
+    k = dev(torch, ok.rate_coefficients(d, T, nH, Av), ld)
+    y = dev(torch, sc.atomic_start(d, C), ld)
+    lib = B.lib()
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    call = lambda C_, k_, y_, ld_, t_: lib.sm_integrate(st.h, C_, k_, y_, ld_, t_, None, stream)
+    kp, yp = ct.c_void_p(k.data_ptr()), ct.c_void_p(y.data_ptr())
+    assert call(0, kp, yp, ld, 1e10) == B.SM_EINVAL          # empty batch
+    assert call(C + 1, kp, yp, ld, 1e10) == B.SM_EINVAL      # beyond the capacity
+    assert call(C, kp, yp, 40, 1e10) == B.SM_EINVAL          # ld not a multiple of 32
+    assert call(C, None, yp, ld, 1e10) == B.SM_EINVAL        # no rate coefficients
+    assert call(C, kp, yp, ld, 0.0) == B.SM_EINVAL           # t_end <= 0
+    for bad in (dict(newton_max=9), dict(q_max=6), dict(rtol=-1.0), dict(refresh_ctas_per_sm=-1)):
+        with pytest.raises(B.StoichError):
+            B.State(net, C, **bad)
+    # the state still integrates after the refused calls
+    assert st.integrate(k, y, 1e5 * YEAR, C) == B.SM_OK
+
+
+def test_single_cell_matches_oracle(torch, B):
+    """The single-cell case (32 x 180, T 10 K, n_H 1e4, A_V 5, atomic start,
+    1e6 yr): a batch of one cell against the oracle's rtol-1e-10 solution,
+    within 10 tolerance units (the oracle's own rtol-1e-6 run is within 2)."""
+    from synth.workloads import WORKLOADS, make
+    w = WORKLOADS["single_cell_32x180"]
+    d, T, nH, Av, y0 = make(w.name)
+    k = ok.rate_coefficients(d, T, nH, Av)
+    ref = ob.integrate_cell(d, k[:, 0], y0[:, 0], w.t_end, ob.BDFOptions(rtol=1e-10, atol=1e-24)).y
+    mine = ob.integrate_cell(d, k[:, 0], y0[:, 0], w.t_end).y
+    e_o = cell_err(mine[:, None], ref[:, None])[0]
+    y, stats, code = run_gpu(torch, B, d, k, y0, w.t_end)
+    assert code == B.SM_OK and stats["status"][0] == B.CELL_OK
+    e_g = cell_err(y, ref[:, None])[0]
+    assert e_o <= 2.0 and e_g <= 10.0, (e_g, e_o)
