@@ -32,7 +32,8 @@ After the headline line's own measurements the same JSON line carries:
   single_cell     the 32 x 180 network, one cell to 1e6 yr (config 0)
   cpu_baseline    the oracle on the host cores: 64 stratified cells, each
                   integrated over the whole interval; beside it the
-                  coupled-temperature oracle on 16 cells and the single cell
+                  coupled-temperature oracle on 16 cells, the single cell
+                  and one right-hand side of the 4096 RHS-workload cells
 
     python bench.py [--gpus N --steps K --warmup W] [--precision mixed|tf32|fp64]
     python bench.py --impl reference ...      # the CPU oracle on a sample
@@ -247,6 +248,23 @@ def _oracle_single_cell():
     return {"workload": w.name, "seconds": time.time() - t0, "steps": int(r.steps)}
 
 
+def _oracle_rhs_config1():
+    """Config 1 on the oracle: one right-hand side of each of the 4096 cells
+    of the RHS workload (dense S @ R over all cells at once, one process);
+    the rate coefficients are inputs, computed before the timed region."""
+    from oracle import kinetics as ok
+    from oracle import network as on
+    from synth.workloads import make
+    d, T, nH, Av, y = make("rhs_jac_470x6000_c4096")
+    k = ok.rate_coefficients(d, T, nH, Av)
+    S = on.stoichiometry(d)
+    t0 = time.time()
+    ok.rhs(d, k, y, S)
+    dt = time.time() - t0
+    return {"workload": "rhs_jac_470x6000_c4096", "cells": int(y.shape[1]), "seconds": dt,
+            "rhs_per_s": y.shape[1] / dt, "sample": "every cell once, one process"}
+
+
 def _pool_init():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
@@ -313,6 +331,7 @@ def cpu_baseline(t_end, thermal_cells=0):
     finally:
         pool.close()
     extra["single_cell"] = _oracle_single_cell()
+    extra["rhs"] = _oracle_rhs_config1()
     return {"value": steps / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle", **extra,
             "sample": (f"{len(cells)} cells of {WORKLOAD} stratified by stiffness (evenly spaced quantiles of "
                        f"the oracle's step count among every 128th of the first 16,384 cells), each integrated "
