@@ -3,17 +3,23 @@
 // machine per cell.
 //
 // One "attempt" advances every unfinished cell by one trial step:
-//   predict   thread per cell: Lagrange predictor, BDF coefficients, weights,
-//             and the decision whether the Newton matrix must be refreshed;
+//   predict   32 cells per CTA, the species split over 8 warps: Lagrange
+//             predictor, BDF coefficients, weights, and the decision whether
+//             the Newton matrix must be refreshed;
 //   refresh   one CTA per cell on the compacted refresh list: J at the
 //             predicted state, M = I - gamma J (FP64, equilibrated and
-//             rounded to FP32 in mixed precision), in-place LU without
-//             pivoting in the minimum-degree order, inverse pivots kept;
+//             rounded to FP32 in mixed precision), LU without pivoting in
+//             the minimum-degree order, written as packed factors;
 //   newton    up to newton_max rounds of: reaction rates + CRS gather of
 //             S R(y) (cells fast axis, masked to iterating cells), then one
 //             warp per cell forming the FP64 residual, forward/backward
 //             substitution and the WRMS convergence test;
-//   finish    thread per cell: error test, order / step selection, history.
+//   finish    32 cells per CTA, the species split over 8 warps: error test,
+//             order / step selection, history.
+// With a coupled temperature (sm_net_set_thermal) the rate coefficients of
+// the T-dependent reactions are recomputed from the state before every
+// right-hand side, the temperature row follows each gather, and T is
+// eliminated last in the Newton solve (th_* kernels below).
 // The host enqueues attempts in groups (captured once in a CUDA graph) and
 // reads back only the number of running cells between groups.  The same file
 // holds the step recording and the discrete adjoint of the frozen-step map
