@@ -330,9 +330,12 @@ __global__ void __launch_bounds__(32 * kCoopWarps) predict_kernel(Dev d) {
 }
 
 // ---------------------------------------------------------------------------
-// refresh: J, M = I - gamma J and its LU without pivoting, in place in dense
-// per-cell storage (elimination order = minimum degree).  One CTA per cell on
-// the compacted refresh list (grid-stride).  With M = [A11 A12; A21 A22]
+// refresh: J, M = I - gamma J and its LU without pivoting (elimination order
+// = minimum degree), worked in a dense matrix (one per refresh CTA, or one
+// per cell in recording states) and written out as the cell's packed
+// factors.  One CTA per cell on the compacted refresh list (grid-stride).
+// The first kJPre term words of the Jacobian entries a thread holds are
+// loaded before any is used.  With M = [A11 A12; A21 A22]
 // split at the first `head` pivots (sparse) and the >= 90 % dense trailing
 // block:
 //  A  dR_j/dx for both reactant slots of every reaction is formed once in
