@@ -203,3 +203,34 @@ def test_synthetic_network_rejects_bad_sizes(B):
     h = ct.c_void_p()
     assert B.lib().sm_net_build_synthetic(1, 8, 100, -1, ct.byref(h)) == B.SM_EINVAL
     assert B.lib().sm_net_build_synthetic(1, 32, 0, -1, ct.byref(h)) == B.SM_EINVAL
+
+
+def test_set_thermal_checks_the_slot_and_parameters(B):
+    """sm_net_set_thermal on the host: the temperature slot must have no
+    atoms, no charge and no reaction; cooling coefficients must be >= 0 with
+    positive excitation temperatures; the constants must be finite and >= 0;
+    NULL turns the mode off."""
+    import dataclasses
+    from synth import thermal as sth
+    d = sth.with_temperature(sn.generate(2312, 32, 180))
+    th = sth.thermal_params(d)
+    net = B.Network(d, device=-1)
+    net.set_thermal(th)                                   # valid
+    net.set_thermal(None)                                 # off
+    bad = [dataclasses.replace(th, t_index=d.species_index("H")),       # has atoms
+           dataclasses.replace(th, t_index=d.species_index("E-")),      # has charge and reactions
+           dataclasses.replace(th, t_index=d.n_s),                      # out of range
+           dataclasses.replace(th, heat=-1.0),
+           dataclasses.replace(th, lam=float("nan")),
+           dataclasses.replace(th, L=np.where(np.arange(d.n_s) == 0, -1.0, th.L)),
+           dataclasses.replace(th, E=np.where(th.L > 0, 0.0, th.E))]
+    for b in bad:
+        with pytest.raises(B.StoichError) as e:
+            net.set_thermal(b)
+        assert e.value.code == B.SM_EINVAL
+    # a species that appears in a reaction cannot be the slot even without atoms
+    d0 = sn.generate(2312, 32, 180)
+    net0 = B.Network(d0, device=-1)
+    with pytest.raises(B.StoichError):
+        net0.set_thermal(dataclasses.replace(th, t_index=d0.species_index("E-"), L=th.L[:d0.n_s],
+                                             E=th.E[:d0.n_s]))
