@@ -98,6 +98,11 @@ def args_():
                    help="expected attempts of one integration; slices are attempts-est / steps long")
     p.add_argument("--time-kernel", default="refresh",
                    choices=["none", "refresh", "rhs", "solve", "predict", "finish"])
+    p.add_argument("--refresh-per-sm", type=int, default=0,
+                   help="cap on resident refresh CTAs per SM for the main integration (0: as many as fit)")
+    p.add_argument("--thermal-time-kernel", default="none",
+                   choices=["none", "refresh", "rhs", "solve", "predict", "finish"],
+                   help="kernel class timed with CUDA events in the coupled-temperature leg")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-pdr", action="store_true", help="skip the PDR-slab simulation")
@@ -682,7 +687,7 @@ def single_cell(B, dev):
     return {"workload": w.name, "gpu_ms": ms, "steps": int(s["steps"][0]), "status": int(code)}
 
 
-def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
+def thermal_leg(B, dev, cells=4096, precisions=("mixed",), time_kernel="none"):
     """Coupled gas temperature (NEXT row: the energy equation as one more BDF
     component, k'(T) re-evaluated inside every Newton iteration): the first
     `cells` cells of the coupled-temperature workload integrated to 1e6 yr
@@ -706,7 +711,7 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
     stream = torch.cuda.current_stream(dev)
     out = {"workload": w.name, "cells": C, "t_end_yr": w.t_end / YEAR}
     for prec in precisions:
-        st = B.State(net, C, precision=prec)
+        st = B.State(net, C, precision=prec, timing_kind=time_kernel)
         st.set_cells(nHd, Avd, None, C)
         stats = B.stats_tensor(C, dev)
         zd = z0d.clone()
@@ -716,7 +721,9 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
             return st.integrate(None, zd, w.t_end, C, stats)
 
         run()
+        st.timing_reset()
         code, ms = timed(run, stream)
+        _, class_ms, class_n = st.timing()
         s = B.stats_to_numpy(stats)
         T1 = zd[th.t_index, :C].cpu().numpy()
         out[prec] = {"seconds": ms * 1e-3, "cell_steps_per_s": float(s["steps"].sum()) / (ms * 1e-3),
@@ -724,6 +731,8 @@ def thermal_leg(B, dev, cells=4096, precisions=("mixed",)):
                      "newton_per_step": float(s["newton_iters"].sum()) / max(float(s["steps"].sum()), 1.0),
                      "cells_ok": int((s["status"] == 0).sum()), "status": int(code),
                      "T_final_K": {"min": float(T1.min()), "median": float(np.median(T1)), "max": float(T1.max())}}
+        if time_kernel != "none":
+            out[prec]["timed_class"] = {"kind": time_kernel, "ms": class_ms, "launches": class_n}
         st.close()
     net.close()
     # the same cells with T held at its initial value (the paper's fixed-T
@@ -931,7 +940,7 @@ def main():
               "mixed": lambda: fp64_vs_mixed(B, a.mixed_cells, dev),
               "adjoint": lambda: adjoint_measurement(B, a.adjoint_cells, dev),
               "probe": lambda: peaks_(B, dev), "pdr": lambda: pdr_slab(B, dev),
-              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells),
+              "thermal": lambda: thermal_leg(B, dev, a.thermal_cells, ("mixed",), a.thermal_time_kernel),
               "single": lambda: single_cell(B, dev)}[a.only]
         if rank == 0:
             print(json.dumps(fn()))
@@ -960,7 +969,8 @@ def main():
         fscr = torch.empty_like(y0d)
         tune = net.autotune(kd, y0d, fscr, C)
         del fscr
-    state = B.State(net, C, precision=a.precision, timing_kind=a.time_kernel)
+    state = B.State(net, C, precision=a.precision, timing_kind=a.time_kernel,
+                    refresh_ctas_per_sm=a.refresh_per_sm)
     stats = B.stats_tensor(C, dev)
     per = state.opts.attempts_per_sync
     A = slice_attempts(a.attempts_est, a.steps, per)
@@ -1071,7 +1081,8 @@ def main():
     adj = aux(adjoint_measurement, B, a.adjoint_cells, dev) if a.adjoint_cells > 0 else None
     rhs = aux(rhs_jac_grid, B, a.rhs_cells, dev, peaks) if a.rhs_cells > 0 else None
     pdr = None if a.no_pdr else aux(pdr_slab, B, dev)
-    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells)
+    therm = None if a.thermal_cells <= 0 else aux(thermal_leg, B, dev, a.thermal_cells, ("mixed",),
+                                                 a.thermal_time_kernel)
     single = aux(single_cell, B, dev)
     cpu = None if a.no_cpu else aux(cpu_baseline, t_end, max(a.thermal_cells, 0))
     out = {
